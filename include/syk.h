@@ -1,0 +1,167 @@
+/*
+ * syk.h -- C ABI of the GB300 (sm_103a) matrix-free Krylov engine for the
+ * Sachdev-Ye-Kitaev model (Kobrin et al., "Many-Body Chaos in the SYK Model").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Model.  H = sum_{i<j<k<l} J_ijkl chi_i chi_j chi_k chi_l (Eq. 1), N even,
+ *   4 <= N <= 64, Majoranas normalised by {chi_i, chi_j} = delta_ij and mapped
+ *   to n = N/2 spins by the Jordan-Wigner map of Supp. Sec. I.A (spin k = bit k
+ *   of the basis index; sigma^y = i sigma^x sigma^z).  Indices are 0-based.
+ * Parity sectors.  H conserves the parity of popcount(x) (Supp. Sec. I.A).
+ *   Sector p in {0 = even, 1 = odd} has dimension D = 2^(n-1); its compact
+ *   index c is the low n-1 bits of x, and x = c | ((popcount(c)+p) & 1) << (n-1).
+ * Vectors.  A batch of B states is stored state-interleaved: element (c, b)
+ *   of a D x B array is at offset c*B + b.  dtype SYK_C64 stores each element
+ *   as two floats (re, im), SYK_C128 as two doubles.  Every scalar reduction
+ *   (Lanczos alpha/beta, dots, norms) and the tridiagonal exponential are FP64
+ *   for both dtypes.
+ * Memory.  Vector arguments are DEVICE pointers owned by the caller unless a
+ *   parameter says "host".  The library owns the term tables (device copies
+ *   are uploaded on first use, on the current device) and its internal
+ *   scratch.  Calls taking `stream` (a cudaStream_t, NULL = legacy default
+ *   stream) are asynchronous unless they return host arrays, which
+ *   synchronise the stream before returning.
+ * Errors.  Every int-returning call returns SYK_OK (0) or a negative code and
+ *   never throws; syk_last_error() gives a message for the calling thread.
+ */
+#ifndef SYK_H
+#define SYK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SYK_OK 0
+#define SYK_EINVAL (-1)   /* bad argument (size, index, dtype, null pointer) */
+#define SYK_ENOMEM (-2)   /* host or device allocation failed, or workspace too small */
+#define SYK_ECUDA (-3)    /* CUDA runtime error (message in syk_last_error) */
+#define SYK_ENUMERIC (-4) /* NaN/Inf in a Lanczos scalar or a non-positive norm where one is needed */
+#define SYK_ETIMEOUT (-5) /* a bounded device-side wait gave up */
+
+#define SYK_C64 1
+#define SYK_C128 2
+
+typedef struct syk_terms syk_terms;
+
+/* ---------------------------------------------------------------- Hamiltonian
+ * syk_build_terms -- Eq. 1 and Supp. Sec. I.A/I.B ("symbolic representation of
+ * H, which contains only O(N^4) terms").  J: host array of C(N,4) real
+ * couplings for i<j<k<l in lexicographic order.  Builds, on the host, the
+ * Pauli string of every term (chi_i chi_j chi_k chi_l = (1/4) i^p X^m Z^z with
+ * X^m Z^z|x> = (-1)^popcount(z&x) |x^m>) and the per-X-mask coefficient
+ * tables the kernels evaluate.  *out is library-owned: free it with
+ * syk_free_terms.  No GPU is touched.  Errors: SYK_EINVAL (N odd, <4, >64,
+ * NULL), SYK_ENOMEM.
+ */
+int syk_build_terms(int N, const double* J, syk_terms** out);
+void syk_free_terms(syk_terms* terms);
+
+/* syk_terms_info -- sizes of a term set (any pointer may be NULL):
+ * N, C(N,4) terms, number of distinct X-masks, sector dimension D. */
+int syk_terms_info(const syk_terms* terms, int* N, int64_t* nterms, int64_t* nmasks, int64_t* dim);
+
+/* syk_term_table -- host copy of the Pauli form of every term, in
+ * lexicographic term order (Supp. Sec. I.A): xmask, zmask (bit k = spin k) and
+ * phase p in 0..3 such that 4 chi_i chi_j chi_k chi_l = i^p X^xmask Z^zmask.
+ * Each output is a caller-owned host array of C(N,4) entries (NULL skips it). */
+int syk_term_table(const syk_terms* terms, uint64_t* xmask, uint64_t* zmask, uint8_t* phase);
+
+/* --------------------------------------------------------------- matvec (K1)
+ * syk_apply_H -- y = H psi in parity sector `parity` (Supp. Sec. I.B: the
+ * matrix-free "core computational component", O(N^4 2^{N/2}) work).
+ * psi, y: device D x batch arrays of `dtype`; must not overlap.  Errors:
+ * SYK_EINVAL, SYK_ECUDA. */
+int syk_apply_H(const syk_terms* terms, int parity, int dtype, const void* psi, void* y,
+                int64_t batch, void* stream);
+
+/* syk_apply_chi -- y = chi_i psi (Supp. Sec. I.A map, with the 1/sqrt(2) that
+ * {chi_i, chi_i} = 1 requires).  psi is in sector parity_in; y is in sector
+ * 1 - parity_in.  Device D x batch arrays; must not overlap. */
+int syk_apply_chi(int N, int i, int parity_in, int dtype, const void* psi, void* y, int64_t batch,
+                  void* stream);
+
+/* --------------------------------------------------------- Krylov (K2 - K4)
+ * syk_tridiag_expm -- the m x m step of the Krylov method (Supp. Sec. I.B:
+ * "exponentiating the projection of H within the subspace"): for each of
+ * `batch` real symmetric tridiagonal matrices T_b (alpha[k*batch+b] on the
+ * diagonal, beta[k*batch+b] for k < m-1 off it) returns
+ * out[k*batch+b] = beta0[b] * (e^{z T_b} e_1)_k as (re, im) doubles.
+ * All pointers are device pointers; 1 <= m <= SYK_MAX_KRYLOV. */
+#define SYK_MAX_KRYLOV 64
+int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const double* beta,
+                     const double* beta0, double z_re, double z_im, double* out, void* stream);
+
+/* syk_workspace_bytes -- device scratch syk_expmv needs for (N, dtype,
+ * krylov_dim, batch): the Krylov basis of krylov_dim+1 vectors, one work
+ * vector and the FP64 scalars.  `kind` is reserved (pass 0). */
+size_t syk_workspace_bytes(int N, int dtype, int krylov_dim, int64_t batch, int kind);
+
+/* syk_expmv -- out = e^{z H} psi in sector `parity` by Lanczos with full
+ * (two-pass classical Gram-Schmidt) reorthogonalisation (Supp. Sec. I.B;
+ * Saad 1992 a-posteriori error estimate).  z = z_re + i z_im: z = -i t for
+ * real time, z = -tau for imaginary time.  Each Krylov basis of dimension
+ * <= krylov_dim (2..SYK_MAX_KRYLOV) advances all states of the batch by a
+ * common sub-step chosen so that the estimated relative error of the step is
+ * <= tol; steps repeat until z is covered ("dividing the time evolution into
+ * a series of small time steps").  A happy breakdown (invariant subspace)
+ * shortens the basis.  workspace: device scratch of ws_bytes >=
+ * syk_workspace_bytes(...), or NULL to let the library allocate it.  psi and
+ * out may be the same array.  *nsteps (may be NULL) receives the number of
+ * Krylov bases used.  Synchronises `stream` once per Krylov basis.
+ * Errors: SYK_EINVAL, SYK_ENOMEM, SYK_ECUDA, SYK_ENUMERIC. */
+int syk_expmv(const syk_terms* terms, int parity, int dtype, double z_re, double z_im,
+              const void* psi, void* out, int64_t batch, int krylov_dim, double tol,
+              void* workspace, size_t ws_bytes, void* stream, int* nsteps);
+
+/* ------------------------------------------------------------- correlators
+ * syk_correlator_G -- real-time two-point function, Eq. G with Eq.
+ * q_typicality: for each of `nstates` states psi~ (in the EVEN sector),
+ * phi = e^{-beta H/2} psi~,
+ * G(t) = <phi| e^{iHt} chi_i e^{-iHt} chi_i |phi> / <phi|phi>  (G_R = 2 Re G).
+ * t: host array of nt >= 1 non-negative, non-decreasing times.  psi0: D x
+ * nstates array, device or host memory (host memory is copied in).  Outputs
+ * are host arrays: G_re_im[(k*nstates + s)*2 + {0,1}] and Z[s] = <phi|phi>.
+ * Synchronises `stream`. */
+int syk_correlator_G(const syk_terms* terms, double beta, int i, const double* t, int nt,
+                     const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
+                     double* G_re_im, double* Z, void* stream);
+
+/* syk_otoc -- regularized OTOC, Eq. F_reg with rho = e^{-beta H} split in four
+ * quarters, estimated with random states (Eq. q_typicality) by the chain
+ *   phi = rho^{1/8} psi~,  a0 = rho^{1/4} chi_j phi,
+ *   p = chi_i U(t) phi,  q = chi_i U(t) a0,  U(t) = e^{-iHt},
+ *   F(t) = < rho^{1/4} U(t)^dag p | chi_j | rho^{1/4} U(t)^dag q >,
+ * which equals <psi~| rho^{1/8} chi_i(t) rho^{1/4} chi_j rho^{1/4} chi_i(t)
+ * rho^{1/4} chi_j rho^{1/8} |psi~> by cyclicity.  i != j.  Unnormalised:
+ * F~(t) = F(t)/F(0).  Same argument conventions as syk_correlator_G;
+ * F_re_im[(k*nstates + s)*2 + {0,1}] (host).  Synchronises `stream`. */
+int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t, int nt,
+             const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
+             double* F_re_im, void* stream);
+
+/* ------------------------------------------------------------- diagnostics
+ * syk_last_error -- message of the last failed call on this thread ("" if none). */
+const char* syk_last_error(void);
+
+/* syk_counters -- counters since the last reset (any pointer may be NULL):
+ * H applications per state (batch counted once per state), Krylov bases.
+ * reset != 0 zeroes them after reading. */
+int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int reset);
+
+/* syk_profile_enable / syk_profile_read -- CUDA-event timing of every apply_H
+ * launch the library makes (on the stream it is launched on).  While enabled,
+ * each launch is bracketed by two events; elapsed times are accumulated when
+ * the library next synchronises (or in syk_profile_read, which synchronises
+ * the device).  Reading returns launches and total milliseconds; reset != 0
+ * zeroes them. */
+int syk_profile_enable(int on);
+int syk_profile_read(int64_t* launches, double* total_ms, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYK_H */

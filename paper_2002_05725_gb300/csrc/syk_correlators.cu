@@ -1,0 +1,204 @@
+// Correlators by random-state typicality (Eq. q_typicality):
+//   G(t)  (Eq. G)      real-time two-point function,
+//   F(t)  (Eq. F_reg)  regularized OTOC with rho^{1/4} between the operators.
+// Each is a host-driven chain of expmv, chi and dot calls on the device; the
+// batch dimension carries the random states of one coupling draw.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "syk_krylov.cuh"
+
+namespace syk {
+namespace {
+
+// Device buffers owned by one correlator call.
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  int alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+      set_error("cannot allocate %zu bytes of device memory: %s", bytes, cudaGetErrorString(e));
+      *p = nullptr;
+      return SYK_ENOMEM;
+    }
+    ptrs.push_back(*p);
+    return SYK_OK;
+  }
+};
+
+int check_common(const syk_terms* t, double beta, const double* times, int nt, const void* psi0, int64_t ns,
+                 int dtype, int kd, double tol, const void* out) {
+  if (!t || !times || !psi0 || !out) {
+    set_error("NULL argument");
+    return SYK_EINVAL;
+  }
+  if (!std::isfinite(beta) || beta < 0.0) {
+    set_error("beta must be finite and >= 0");
+    return SYK_EINVAL;
+  }
+  if (nt < 1 || ns < 1 || ns > 256 || kd < 2 || kd > SYK_MAX_KRYLOV || !dtype_ok(dtype) || !(tol > 0.0)) {
+    set_error("invalid sizes (nt=%d nstates=%lld krylov_dim=%d dtype=%d tol=%g)", nt, (long long)ns, kd, dtype, tol);
+    return SYK_EINVAL;
+  }
+  double prev = 0.0;
+  for (int k = 0; k < nt; ++k) {
+    if (!std::isfinite(times[k]) || times[k] < prev) {
+      set_error("times must be finite, >= 0 and non-decreasing");
+      return SYK_EINVAL;
+    }
+    prev = times[k];
+  }
+  return SYK_OK;
+}
+
+// Returns a device copy of psi0 if it is host memory, else psi0 itself.
+int device_input(const void* psi0, size_t bytes, Scratch& sc, const void** out) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, psi0);
+  if (e != cudaSuccess) cudaGetLastError();
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+    *out = psi0;
+    return SYK_OK;
+  }
+  void* d = nullptr;
+  SYK_TRY(sc.alloc(&d, bytes));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(d, psi0, bytes, cudaMemcpyHostToDevice, sc.st));
+  *out = d;
+  return SYK_OK;
+}
+
+}  // namespace
+}  // namespace syk
+
+using namespace syk;
+
+extern "C" int syk_correlator_G(const syk_terms* terms, double beta, int i, const double* t, int nt, const void* psi0,
+                                int64_t nstates, int dtype, int krylov_dim, double tol, double* G_re_im, double* Z,
+                                void* stream) {
+  clear_error();
+  SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, G_re_im));
+  if (i < 0 || i >= terms->N) {
+    set_error("syk_correlator_G: Majorana index %d out of range", i);
+    return SYK_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t B = nstates;
+  ApplyParams P0, P1;
+  SYK_TRY(make_apply_params(terms, 0, dtype, &P0));
+  SYK_TRY(make_apply_params(terms, 1, dtype, &P1));
+  Scratch sc(st);
+  const size_t vb = size_t(terms->D) * B * dtype_size(dtype);
+  const size_t wsb = krylov_ws_bytes(terms->D, dtype, krylov_dim, B);
+  void *wsp, *a, *b, *tmp, *res;
+  SYK_TRY(sc.alloc(&wsp, wsb));
+  SYK_TRY(sc.alloc(&a, vb));
+  SYK_TRY(sc.alloc(&b, vb));
+  SYK_TRY(sc.alloc(&tmp, vb));
+  SYK_TRY(sc.alloc(&res, sizeof(double2) * B * (nt + 1)));
+  const void* psi = nullptr;
+  SYK_TRY(device_input(psi0, vb, sc, &psi));
+  KrylovWS ws;
+  SYK_TRY(krylov_ws_carve(&ws, wsp, wsb, terms->D, dtype, krylov_dim, B));
+  double2* r = static_cast<double2*>(res);
+  // phi = e^{-beta H/2} psi~ (even sector), Z = <phi|phi>
+  SYK_TRY(expmv_impl(P0, dtype, {-0.5 * beta, 0.0}, psi, a, B, tol, ws, st, nullptr));
+  SYK_TRY(dot_columns(a, a, terms->D, B, dtype, ws, r + size_t(nt) * B, st));
+  SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, a, b, B, st));  // b = chi_i phi (odd)
+  double tcur = 0.0;
+  for (int k = 0; k < nt; ++k) {
+    const double dt = t[k] - tcur;
+    if (dt > 0.0) {
+      SYK_TRY(expmv_impl(P0, dtype, {0.0, -dt}, a, a, B, tol, ws, st, nullptr));
+      SYK_TRY(expmv_impl(P1, dtype, {0.0, -dt}, b, b, B, tol, ws, st, nullptr));
+      tcur = t[k];
+    }
+    SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, b, tmp, B, st));  // chi_i U chi_i phi (even)
+    SYK_TRY(dot_columns(a, tmp, terms->D, B, dtype, ws, r + size_t(k) * B, st));
+  }
+  std::vector<double2> h(size_t(nt + 1) * B);
+  SYK_CUDA_CHECK(cudaMemcpyAsync(h.data(), r, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  prof_collect();
+  for (int64_t s = 0; s < B; ++s) {
+    const double z = h[size_t(nt) * B + s].x;
+    if (Z) Z[s] = z;
+    for (int k = 0; k < nt; ++k) {
+      const double2 v = h[size_t(k) * B + s];
+      G_re_im[(size_t(k) * B + s) * 2] = z > 0 ? v.x / z : NAN;
+      G_re_im[(size_t(k) * B + s) * 2 + 1] = z > 0 ? v.y / z : NAN;
+    }
+  }
+  return SYK_OK;
+}
+
+extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t, int nt, const void* psi0,
+                        int64_t nstates, int dtype, int krylov_dim, double tol, double* F_re_im, void* stream) {
+  clear_error();
+  SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im));
+  if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
+    set_error("syk_otoc: need 0 <= i != j < N (i=%d j=%d)", i, j);
+    return SYK_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t B = nstates;
+  ApplyParams P0, P1;
+  SYK_TRY(make_apply_params(terms, 0, dtype, &P0));
+  SYK_TRY(make_apply_params(terms, 1, dtype, &P1));
+  Scratch sc(st);
+  const size_t vb = size_t(terms->D) * B * dtype_size(dtype);
+  const size_t wsb = krylov_ws_bytes(terms->D, dtype, krylov_dim, B);
+  void *wsp, *ua, *ub, *pr, *qs, *tmp, *res;
+  SYK_TRY(sc.alloc(&wsp, wsb));
+  SYK_TRY(sc.alloc(&ua, vb));
+  SYK_TRY(sc.alloc(&ub, vb));
+  SYK_TRY(sc.alloc(&pr, vb));
+  SYK_TRY(sc.alloc(&qs, vb));
+  SYK_TRY(sc.alloc(&tmp, vb));
+  SYK_TRY(sc.alloc(&res, sizeof(double2) * B * nt));
+  const void* psi = nullptr;
+  SYK_TRY(device_input(psi0, vb, sc, &psi));
+  KrylovWS ws;
+  SYK_TRY(krylov_ws_carve(&ws, wsp, wsb, terms->D, dtype, krylov_dim, B));
+  double2* r = static_cast<double2*>(res);
+  const std::complex<double> q8(-beta / 8.0, 0.0), q4(-beta / 4.0, 0.0);
+  // ua = phi = rho^{1/8} psi~ (even); ub = a0 = rho^{1/4} chi_j phi (odd)
+  SYK_TRY(expmv_impl(P0, dtype, q8, psi, ua, B, tol, ws, st, nullptr));
+  SYK_TRY(launch_apply_chi(terms->N, j, 0, dtype, ua, tmp, B, st));
+  SYK_TRY(expmv_impl(P1, dtype, q4, tmp, ub, B, tol, ws, st, nullptr));
+  double tcur = 0.0;
+  for (int k = 0; k < nt; ++k) {
+    const double tk = t[k], dt = tk - tcur;
+    if (dt > 0.0) {
+      SYK_TRY(expmv_impl(P0, dtype, {0.0, -dt}, ua, ua, B, tol, ws, st, nullptr));  // U(t) phi
+      SYK_TRY(expmv_impl(P1, dtype, {0.0, -dt}, ub, ub, B, tol, ws, st, nullptr));  // U(t) a0
+      tcur = tk;
+    }
+    SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, ua, pr, B, st));  // p (odd)
+    SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, ub, qs, B, st));  // q (even)
+    if (tk > 0.0) {
+      SYK_TRY(expmv_impl(P1, dtype, {0.0, tk}, pr, pr, B, tol, ws, st, nullptr));  // U^dag p
+      SYK_TRY(expmv_impl(P0, dtype, {0.0, tk}, qs, qs, B, tol, ws, st, nullptr));  // U^dag q
+    }
+    SYK_TRY(expmv_impl(P1, dtype, q4, pr, pr, B, tol, ws, st, nullptr));  // r
+    SYK_TRY(expmv_impl(P0, dtype, q4, qs, qs, B, tol, ws, st, nullptr));  // s
+    SYK_TRY(launch_apply_chi(terms->N, j, 0, dtype, qs, tmp, B, st));     // chi_j s (odd)
+    SYK_TRY(dot_columns(pr, tmp, terms->D, B, dtype, ws, r + size_t(k) * B, st));
+  }
+  std::vector<double2> h(size_t(nt) * B);
+  SYK_CUDA_CHECK(cudaMemcpyAsync(h.data(), r, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  prof_collect();
+  for (size_t e = 0; e < h.size(); ++e) {
+    F_re_im[2 * e] = h[e].x;
+    F_re_im[2 * e + 1] = h[e].y;
+  }
+  return SYK_OK;
+}

@@ -1,0 +1,94 @@
+// Internal declarations shared by the translation units of libsyk_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/syk.h"
+
+namespace syk {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define SYK_CUDA_CHECK(expr)                                                                   \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      syk::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return SYK_ECUDA;                                                                        \
+    }                                                                                          \
+  } while (0)
+
+#define SYK_TRY(expr)          \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != SYK_OK) return rc_; \
+  } while (0)
+
+// Device copies of the grouped coefficient tables (see syk_terms.cpp for the math).
+struct DeviceTables {
+  int device = -1;
+  uint4* m4_rec = nullptr;    // popcount-4 X-masks: {compact xor, zeta0, packed support, 0}
+  double2* m4_t64 = nullptr;  // 32 entries per mask: T[u], then -T[u]
+  float2* m4_t32 = nullptr;
+  uint4* m2_rec = nullptr;    // popcount-2 X-masks: {compact xor, zeta_f, a | b<<8, 0}
+  double2* m2_t64 = nullptr;  // n x 4 entries per mask: W_c[u]
+  float2* m2_t32 = nullptr;
+  double* wd64 = nullptr;     // n x n upper triangle: diagonal couplings w_cd
+  float* wd32 = nullptr;
+};
+
+// Everything apply_H needs, by value, for one launch.
+struct ApplyParams {
+  int n;        // spins
+  int sector;   // 0 even, 1 odd
+  int64_t D;    // sector dimension 2^(n-1)
+  int n4, n2;
+  const uint4* m4_rec;
+  const uint4* m2_rec;
+  const void* m4_tab;
+  const void* m2_tab;
+  const void* wd;
+};
+
+int ensure_device_tables(const syk_terms* t);
+int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p);
+
+// Kernel launchers (stream-ordered, no synchronisation).
+int launch_apply_H(const ApplyParams& p, int dtype, const void* psi, void* y, int64_t batch,
+                   cudaStream_t st);
+int launch_apply_chi(int N, int i, int parity_in, int dtype, const void* psi, void* y,
+                     int64_t batch, cudaStream_t st);
+
+// Profiling of apply_H launches (CUDA events) and work counters.
+void prof_before_apply(cudaStream_t st);
+void prof_after_apply(cudaStream_t st);
+void prof_collect();
+void count_applies(int64_t states);
+void count_bases(int64_t n);
+
+inline size_t dtype_size(int dtype) { return dtype == SYK_C64 ? 8 : 16; }
+inline bool dtype_ok(int dtype) { return dtype == SYK_C64 || dtype == SYK_C128; }
+
+}  // namespace syk
+
+struct syk_terms {
+  int N = 0, n = 0;
+  int64_t nterms = 0, D = 0;
+  std::vector<uint64_t> xm, zm;  // per term, lexicographic order
+  std::vector<uint8_t> ph;
+  std::vector<double> J;
+  int n4 = 0, n2 = 0;
+  std::vector<uint32_t> m4_rec;  // 4 words per mask
+  std::vector<double> m4_tab;    // n4 * 32 * 2
+  std::vector<uint32_t> m2_rec;  // 4 words per mask
+  std::vector<double> m2_tab;    // n2 * n * 4 * 2
+  std::vector<double> wdiag;     // n * n
+  mutable syk::DeviceTables dev;
+  mutable std::mutex mtx;
+};

@@ -1,0 +1,672 @@
+// Krylov expmv (Supp. Sec. I.B): Lanczos basis with two-pass classical
+// Gram-Schmidt reorthogonalisation (K2 + K7), eigendecomposition of the FP64
+// tridiagonal projection and its exponential (K3), and the combination
+// psi_out = V c (K4).  All scalars are FP64; complex64 vectors use FP32
+// arithmetic with FP64 accumulation of every reduction.
+//
+// Vector kernels use blockDim = B * floor(256/B) threads, so thread t always
+// works on batch column t % B, and a fixed number G of blocks; each block
+// writes one partial sum per (vector, column), summed in a fixed order by a
+// second kernel (results are deterministic).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "syk_cplx.cuh"
+#include "syk_krylov.cuh"
+
+namespace syk {
+namespace {
+
+constexpr int kMaxRedBlocks = 304;  // 2 x 152 SMs
+constexpr int kFlush = 16;          // FP32 partial sums are flushed to FP64 every kFlush elements
+
+inline int vec_bdim(int64_t B) { return int(B) * std::max(1, int(256 / B)); }
+inline int red_grid(int64_t total, int bdim) {
+  return int(std::min<int64_t>((total + bdim - 1) / bdim, kMaxRedBlocks));
+}
+
+// ---------------------------------------------------------------- reductions
+// Accumulates sum conj(a) * b.  FP32 data: products and short partial sums in
+// FP32, flushed into FP64 every kFlush elements.  FP64 data: FP64 throughout.
+template <typename R>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double re = 0, im = 0;
+  __device__ void add(double2 a, double2 b) {
+    re = fma(a.x, b.x, fma(a.y, b.y, re));
+    im = fma(a.x, b.y, fma(-a.y, b.x, im));
+  }
+  __device__ void tick() {}
+  __device__ double2 get() { return make_double2(re, im); }
+};
+template <>
+struct DotAcc<float> {
+  double re = 0, im = 0;
+  float fr = 0.f, fi = 0.f;
+  int cnt = 0;
+  __device__ void add(float2 a, float2 b) {
+    fr = fmaf(a.x, b.x, fmaf(a.y, b.y, fr));
+    fi = fmaf(a.x, b.y, fmaf(-a.y, b.x, fi));
+  }
+  __device__ void tick() {
+    if (++cnt == kFlush) {
+      re += fr;
+      im += fi;
+      fr = fi = 0.f;
+      cnt = 0;
+    }
+  }
+  __device__ double2 get() { return make_double2(re + fr, im + fi); }
+};
+
+// Block-level reduction of one double2 per thread into one value per column:
+// thread t < B gets the sum over threads t, t+B, t+2B, ... in that order.
+__device__ double2 block_reduce_cols(double2 v, int B, double2* sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  double2 r = make_double2(0.0, 0.0);
+  if ((int)threadIdx.x < B) {
+    for (int t = threadIdx.x; t < (int)blockDim.x; t += B) {
+      r.x += sm[t].x;
+      r.y += sm[t].y;
+    }
+  }
+  __syncthreads();
+  return r;
+}
+
+// part[(k*G + g)*B + b] = sum over this block's elements of conj(V_k) w
+template <typename R>
+__global__ void k_dots(int nk0, const typename CT<R>::T* __restrict__ V, size_t vs,
+                       const typename CT<R>::T* __restrict__ w, int64_t total, int B, double2* __restrict__ part) {
+  extern __shared__ double2 sm[];
+  const int k = nk0 + blockIdx.y;
+  const typename CT<R>::T* __restrict__ v = V + (size_t)k * vs;
+  DotAcc<R> acc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    acc.add(v[e], w[e]);
+    acc.tick();
+  }
+  double2 r = block_reduce_cols(acc.get(), B, sm);
+  if ((int)threadIdx.x < B) part[((size_t)k * gridDim.x + blockIdx.x) * B + threadIdx.x] = r;
+}
+
+__global__ void k_reduce_parts(int nk, int G, int B, const double2* __restrict__ part, double2* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nk * B) return;
+  const int k = idx / B, b = idx - k * B;
+  double2 s = make_double2(0.0, 0.0);
+  for (int g = 0; g < G; ++g) {
+    const double2 p = part[((size_t)k * G + g) * B + b];
+    s.x += p.x;
+    s.y += p.y;
+  }
+  out[idx] = s;
+}
+
+// w -= sum_{k<nk} h_k V_k (per column); npart[g*B + b] = partial |w|^2 of the result
+template <typename R>
+__global__ void k_update(int nk, const typename CT<R>::T* __restrict__ V, size_t vs, const double2* __restrict__ h,
+                         typename CT<R>::T* __restrict__ w, int64_t total, int B, double* __restrict__ npart) {
+  using C = typename CT<R>::T;
+  extern __shared__ double2 sm[];
+  const int b = threadIdx.x % B;
+  DotAcc<R> acc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    C x = w[e];
+    for (int k = 0; k < nk; ++k) {
+      const double2 hk = h[k * B + b];
+      const C v = V[(size_t)k * vs + e];
+      cmac(x, R(-hk.x), R(-hk.y), v);
+    }
+    w[e] = x;
+    acc.add(x, x);
+    acc.tick();
+  }
+  double2 r = block_reduce_cols(acc.get(), B, sm);
+  if ((int)threadIdx.x < B && npart) npart[(size_t)blockIdx.x * B + threadIdx.x] = r.x;
+}
+
+template <typename R>
+__global__ void k_scale(const typename CT<R>::T* __restrict__ src, typename CT<R>::T* __restrict__ dst,
+                        const double* __restrict__ inv, int64_t total, int B) {
+  const int b = threadIdx.x % B;
+  const R s = R(inv[b]);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    typename CT<R>::T v = src[e];
+    v.x *= s;
+    v.y *= s;
+    dst[e] = v;
+  }
+}
+
+// out = sum_{k<nk} c_k V_k (per column)
+template <typename R>
+__global__ void k_combine(int nk, const typename CT<R>::T* __restrict__ V, size_t vs, const double2* __restrict__ c,
+                          typename CT<R>::T* __restrict__ out, int64_t total, int B) {
+  using C = typename CT<R>::T;
+  const int b = threadIdx.x % B;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    C x = make_c<R>(R(0), R(0));
+    for (int k = 0; k < nk; ++k) {
+      const double2 ck = c[k * B + b];
+      cmac(x, R(ck.x), R(ck.y), V[(size_t)k * vs + e]);
+    }
+    out[e] = x;
+  }
+}
+
+// beta0 = ||psi||, inv = 1/beta0 (0 for a zero column)
+__global__ void k_norm_init(int B, const double2* __restrict__ d, double* __restrict__ beta0, double* __restrict__ inv,
+                            int* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double n2 = d[b].x;
+  const double nb = sqrt(fmax(n2, 0.0));
+  if (!isfinite(nb)) atomicOr(status, 1);
+  beta0[b] = nb;
+  inv[b] = nb > 0.0 ? 1.0 / nb : 0.0;
+}
+
+// alpha_j = Re(h1_j + h2_j), beta_j = ||w||; breakdown sets beta_j = 0
+__global__ void k_lanczos_scalars(int j, int B, int G, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                                  const double* __restrict__ npart, double* __restrict__ alpha,
+                                  double* __restrict__ beta, double* __restrict__ inv, int* status, double bt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double a = h1[j * B + b].x + h2[j * B + b].x;
+  double n2 = 0.0;
+  for (int g = 0; g < G; ++g) n2 += npart[(size_t)g * B + b];
+  double be = sqrt(fmax(n2, 0.0));
+  if (!isfinite(a) || !isfinite(be)) {
+    atomicOr(status, 1);
+    be = 0.0;
+  }
+  const double prev = j > 0 ? beta[(j - 1) * B + b] : 0.0;
+  if (be <= bt * (fabs(a) + prev)) be = 0.0;
+  alpha[j * B + b] = isfinite(a) ? a : 0.0;
+  beta[j * B + b] = be;
+  inv[b] = be > 0.0 ? 1.0 / be : 0.0;
+}
+
+// ---------------------------------------------------------------- tridiagonal
+// Implicit symmetric QR with Wilkinson shift (Golub & Van Loan, Sec. 8.3) on
+// T = tridiag(beta, alpha, beta) of dimension m, one warp per matrix.  Lane 0
+// computes every Givens rotation (the scalar recurrence), all lanes apply it
+// to their rows of the accumulated eigenvector matrix Q (row-major m x m in
+// shared memory).  On return d holds the eigenvalues and T = Q diag(d) Q^T.
+__device__ bool tridiag_eig_warp(int m, double* d, double* e, double* Q, double* rot) {
+  const int lane = threadIdx.x & 31;
+  for (int r = lane; r < m; r += 32)
+    for (int c = 0; c < m; ++c) Q[r * m + c] = (r == c) ? 1.0 : 0.0;
+  __syncwarp();
+  const double eps = 2.220446049250313e-16;
+  int q = m - 1;
+  int iter = 0;
+  bool ok = true;
+  while (q > 0) {
+    if (fabs(e[q - 1]) <= eps * (fabs(d[q - 1]) + fabs(d[q]))) {
+      --q;
+      continue;
+    }
+    if (++iter > 64 * m) {
+      ok = false;
+      break;
+    }
+    int l = q - 1;
+    while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
+    double x = 0.0, y = 0.0;
+    if (lane == 0) {
+      const double dd = 0.5 * (d[q - 1] - d[q]);
+      const double ee = e[q - 1];
+      const double mu = d[q] - ee * ee / (dd + copysign(hypot(dd, ee), dd));
+      x = d[l] - mu;
+      y = e[l];
+    }
+    for (int k = l; k < q; ++k) {
+      if (lane == 0) {
+        const double r = hypot(x, y);
+        const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? y / r : 0.0;
+        if (k > l) e[k - 1] = r;
+        const double a = d[k], b = e[k], cc = d[k + 1];
+        d[k] = c * c * a + 2.0 * c * s * b + s * s * cc;
+        d[k + 1] = s * s * a - 2.0 * c * s * b + c * c * cc;
+        e[k] = c * s * (cc - a) + (c * c - s * s) * b;
+        if (k + 1 < q) {
+          y = s * e[k + 1];
+          e[k + 1] = c * e[k + 1];
+          x = e[k];
+        }
+        rot[0] = c;
+        rot[1] = s;
+      }
+      __syncwarp();
+      const double c = rot[0], s = rot[1];
+      for (int r = lane; r < m; r += 32) {
+        const double qa = Q[r * m + k], qb = Q[r * m + k + 1];
+        Q[r * m + k] = c * qa + s * qb;
+        Q[r * m + k + 1] = -s * qa + c * qb;
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  return ok;
+}
+
+__device__ __forceinline__ double2 cexp_scaled(double s, double zr, double zi, double th) {
+  const double mag = exp(s * zr * th);
+  double sn, cs;
+  sincos(s * zi * th, &sn, &cs);
+  return make_double2(mag * cs, mag * sn);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Saad's estimate of the relative error of the step s: beta_last |e_m^T e^{szT} e_1| / ||e^{szT} e_1||
+__device__ double step_error(int m, const double* d, const double* Q, double beta_last, double s, double zr, double zi) {
+  if (beta_last == 0.0) return 0.0;
+  const int lane = threadIdx.x & 31;
+  double nr = 0.0, ni = 0.0, den = 0.0;
+  for (int k = lane; k < m; k += 32) {
+    const double2 f = cexp_scaled(s, zr, zi, d[k]);
+    const double g = Q[k], h = Q[(m - 1) * m + k];
+    nr += h * g * f.x;
+    ni += h * g * f.y;
+    den += (f.x * f.x + f.y * f.y) * g * g;
+  }
+  nr = warp_sum(nr);
+  ni = warp_sum(ni);
+  den = warp_sum(den);
+  if (!(den > 0.0)) return 0.0;
+  return beta_last * sqrt(nr * nr + ni * ni) / sqrt(den);
+}
+
+// One block (one warp) per batch column: eigendecomposition of T_b and the
+// largest s <= s_target whose error estimate is <= tol.
+__global__ void k_tridiag_eig(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
+                              const double* __restrict__ beta_last_arr, double zr, double zi, double s_target,
+                              double tol, double* __restrict__ theta, double* __restrict__ Qout,
+                              double* __restrict__ sb, int* status) {
+  extern __shared__ double smd[];
+  double* Q = smd;
+  double* d = Q + m * m;
+  double* e = d + m;
+  double* rot = e + m;
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x;
+  for (int k = lane; k < m; k += 32) {
+    d[k] = alpha[k * B + b];
+    e[k] = k + 1 < m ? beta[k * B + b] : 0.0;
+  }
+  __syncwarp();
+  const bool ok = tridiag_eig_warp(m, d, e, Q, rot);
+  if (!ok && lane == 0) atomicOr(status, 2);
+  const double bl = beta_last_arr ? beta_last_arr[b] : 0.0;
+  double s = s_target;
+  if (step_error(m, d, Q, bl, s, zr, zi) > tol) {
+    double lo = 0.0, hi = s;
+    s *= 0.5;
+    int it = 0;
+    while (step_error(m, d, Q, bl, s, zr, zi) > tol && it < 80) {
+      hi = s;
+      s *= 0.5;
+      ++it;
+    }
+    lo = s;
+    for (int k = 0; k < 24; ++k) {  // largest admissible step within [lo, hi)
+      const double mid = 0.5 * (lo + hi);
+      if (step_error(m, d, Q, bl, mid, zr, zi) <= tol) lo = mid;
+      else hi = mid;
+    }
+    s = lo;
+  }
+  for (int k = lane; k < m; k += 32) theta[k * B + b] = d[k];
+  for (int r = lane; r < m; r += 32)
+    for (int c = 0; c < m; ++c) Qout[((size_t)b * m + r) * m + c] = Q[r * m + c];
+  if (lane == 0) sb[b] = s;
+}
+
+__global__ void k_step_min(int B, const double* __restrict__ sb, double* __restrict__ sacc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = sb[0];
+    for (int b = 1; b < B; ++b) s = fmin(s, sb[b]);
+    *sacc = s;
+  }
+}
+
+// c[k*B + b] = beta0_b * sum_l Q_b[k][l] e^{s z theta_l} Q_b[0][l]
+__global__ void k_tridiag_coef(int m, int B, const double* __restrict__ theta, const double* __restrict__ Q,
+                               const double* __restrict__ beta0, double zr, double zi, const double* __restrict__ sptr,
+                               double s_val, double2* __restrict__ c) {
+  __shared__ double2 fg[SYK_MAX_KRYLOV];
+  const int b = blockIdx.x;
+  const int k = threadIdx.x;
+  const double s = sptr ? *sptr : s_val;
+  const double* Qb = Q + (size_t)b * m * m;
+  if (k < m) {
+    const double2 f = cexp_scaled(s, zr, zi, theta[k * B + b]);
+    const double g = Qb[k];  // row 0
+    fg[k] = make_double2(f.x * g, f.y * g);
+  }
+  __syncthreads();
+  if (k < m) {
+    double re = 0.0, im = 0.0;
+    for (int l = 0; l < m; ++l) {
+      const double q = Qb[k * m + l];
+      re = fma(q, fg[l].x, re);
+      im = fma(q, fg[l].y, im);
+    }
+    const double b0 = beta0[b];
+    c[k * B + b] = make_double2(b0 * re, b0 * im);
+  }
+}
+
+// ---------------------------------------------------------------- launch helpers
+template <typename R>
+struct Ops {
+  using C = typename CT<R>::T;
+  static void dots(const KrylovWS& ws, int k0, int nk, const void* V, size_t vs, const void* w, cudaStream_t st) {
+    dim3 grid(ws.G, nk);
+    k_dots<R><<<grid, ws.bdim, ws.bdim * sizeof(double2), st>>>(k0, (const C*)V, vs, (const C*)w, ws.D * ws.B,
+                                                                 (int)ws.B, ws.part);
+  }
+  static void update(const KrylovWS& ws, int nk, const void* V, size_t vs, const double2* h, void* w, double* np,
+                     cudaStream_t st) {
+    k_update<R><<<ws.G, ws.bdim, ws.bdim * sizeof(double2), st>>>(nk, (const C*)V, vs, h, (C*)w, ws.D * ws.B,
+                                                                   (int)ws.B, np);
+  }
+  static void scale(const KrylovWS& ws, const void* src, void* dst, const double* inv, cudaStream_t st) {
+    k_scale<R><<<ws.G, ws.bdim, 0, st>>>((const C*)src, (C*)dst, inv, ws.D * ws.B, (int)ws.B);
+  }
+  static void combine(const KrylovWS& ws, int nk, const double2* c, void* out, cudaStream_t st) {
+    k_combine<R><<<ws.G, ws.bdim, 0, st>>>(nk, (const C*)ws.V, (size_t)(ws.D * ws.B), c, (C*)out, ws.D * ws.B,
+                                           (int)ws.B);
+  }
+};
+
+void reduce_parts(const KrylovWS& ws, int nk, double2* out, cudaStream_t st) {
+  const int n = nk * (int)ws.B;
+  k_reduce_parts<<<(n + 127) / 128, 128, 0, st>>>(nk, ws.G, (int)ws.B, ws.part, out);
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- workspace
+size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B) {
+  const int bdim = vec_bdim(B);
+  const int G = red_grid(D * B, bdim);
+  const size_t vb = align_up(size_t(D) * B * dtype_size(dtype));
+  size_t s = 0;
+  s += vb * (m + 1);                                  // V
+  s += vb;                                            // w
+  s += align_up(sizeof(double2) * G * (m + 1) * B);   // part
+  s += 2 * align_up(sizeof(double2) * (m + 1) * B);   // h1, h2
+  s += align_up(sizeof(double) * G * B);              // npart
+  s += 2 * align_up(sizeof(double) * m * B);          // alpha, beta
+  s += 3 * align_up(sizeof(double) * B);              // beta0, inv, sb
+  s += align_up(sizeof(double) * m * B);              // theta
+  s += align_up(sizeof(double) * m * m * B);          // Q
+  s += align_up(sizeof(double));                      // sacc
+  s += align_up(sizeof(double2) * m * B);             // c
+  s += align_up(sizeof(int) * 4);                     // status
+  return s;
+}
+
+int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype, int m, int64_t B) {
+  if (bytes < krylov_ws_bytes(D, dtype, m, B)) {
+    set_error("workspace too small: %zu < %zu bytes", bytes, krylov_ws_bytes(D, dtype, m, B));
+    return SYK_ENOMEM;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 255) != 0) {
+    set_error("workspace must be 256-byte aligned");
+    return SYK_EINVAL;
+  }
+  ws->m = m;
+  ws->B = B;
+  ws->D = D;
+  ws->dtype = dtype;
+  ws->bdim = vec_bdim(B);
+  ws->G = red_grid(D * B, ws->bdim);
+  const size_t vb = align_up(size_t(D) * B * dtype_size(dtype));
+  char* p = static_cast<char*>(base);
+  auto take = [&](size_t n) {
+    char* r = p;
+    p += align_up(n);
+    return r;
+  };
+  ws->V = take(vb * (m + 1));
+  ws->w = take(vb);
+  ws->part = (double2*)take(sizeof(double2) * ws->G * (m + 1) * B);
+  ws->h1 = (double2*)take(sizeof(double2) * (m + 1) * B);
+  ws->h2 = (double2*)take(sizeof(double2) * (m + 1) * B);
+  ws->npart = (double*)take(sizeof(double) * ws->G * B);
+  ws->alpha = (double*)take(sizeof(double) * m * B);
+  ws->beta = (double*)take(sizeof(double) * m * B);
+  ws->beta0 = (double*)take(sizeof(double) * B);
+  ws->inv = (double*)take(sizeof(double) * B);
+  ws->sb = (double*)take(sizeof(double) * B);
+  ws->theta = (double*)take(sizeof(double) * m * B);
+  ws->Q = (double*)take(sizeof(double) * m * m * B);
+  ws->sacc = (double*)take(sizeof(double));
+  ws->c = (double2*)take(sizeof(double2) * m * B);
+  ws->status = (int*)take(sizeof(int) * 4);
+  return SYK_OK;
+}
+
+// ---------------------------------------------------------------- dot helper
+int dot_columns(const void* x, const void* y, int64_t D, int64_t B, int dtype, KrylovWS& ws, double2* res,
+                cudaStream_t st) {
+  if (ws.D != D || ws.B != B || ws.dtype != dtype) {
+    set_error("dot_columns: workspace shape mismatch");
+    return SYK_EINVAL;
+  }
+  if (dtype == SYK_C64) Ops<float>::dots(ws, 0, 1, x, 0, y, st);
+  else Ops<double>::dots(ws, 0, 1, x, 0, y, st);
+  reduce_parts(ws, 1, res, st);
+  SYK_CUDA_CHECK(cudaGetLastError());
+  return SYK_OK;
+}
+
+// ---------------------------------------------------------------- expmv
+namespace {
+
+template <typename R>
+int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, void* out, double tol,
+            KrylovWS& ws, cudaStream_t st, int* nsteps) {
+  const int64_t B = ws.B;
+  const size_t vs = size_t(ws.D) * B;
+  const int m = ws.m;
+  const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
+  const double zr = z.real(), zi = z.imag();
+  int* hstat = static_cast<int*>(pinned_scratch(64));
+  double* hs = reinterpret_cast<double*>(hstat + 4);
+  SYK_CUDA_CHECK(cudaMemsetAsync(ws.status, 0, sizeof(int) * 4, st));
+  double s_rem = 1.0;
+  int steps = 0;
+  const void* cur = psi;
+  while (s_rem > 0.0) {
+    if (++steps > 100000) {
+      set_error("expmv: more than 100000 Krylov steps");
+      return SYK_ENUMERIC;
+    }
+    // v_0 = cur / ||cur||
+    Ops<R>::dots(ws, 0, 1, cur, 0, cur, st);
+    reduce_parts(ws, 1, ws.h1, st);
+    k_norm_init<<<(int(B) + 127) / 128, 128, 0, st>>>(int(B), ws.h1, ws.beta0, ws.inv, ws.status);
+    Ops<R>::scale(ws, cur, ws.vec(0), ws.inv, st);
+    int m_eff = m;
+    for (int j = 0; j < m; ++j) {
+      SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, B, st));
+      // first Gram-Schmidt pass
+      Ops<R>::dots(ws, 0, j + 1, ws.V, vs, ws.w, st);
+      reduce_parts(ws, j + 1, ws.h1, st);
+      Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, nullptr, st);
+      // second pass
+      Ops<R>::dots(ws, 0, j + 1, ws.V, vs, ws.w, st);
+      reduce_parts(ws, j + 1, ws.h2, st);
+      Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
+      k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, ws.h2, ws.npart, ws.alpha,
+                                                               ws.beta, ws.inv, ws.status, bt);
+      if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
+      const bool last = (j + 1 == m);
+      if (last || ((j + 1) % 8 == 0)) {
+        const int mm = j + 1;
+        const size_t smem = sizeof(double) * (size_t(mm) * mm + 2 * mm + 2);
+        k_tridiag_eig<<<int(B), 32, smem, st>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem,
+                                                tol, ws.theta, ws.Q, ws.sb, ws.status);
+        k_step_min<<<1, 32, 0, st>>>(int(B), ws.sb, ws.sacc);
+        SYK_CUDA_CHECK(cudaMemcpyAsync(hstat, ws.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+        SYK_CUDA_CHECK(cudaMemcpyAsync(hs, ws.sacc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+        prof_collect();
+        if (hstat[0] & 1) {
+          set_error("expmv: non-finite Lanczos scalar");
+          return SYK_ENUMERIC;
+        }
+        if (hstat[0] & 2) {
+          set_error("expmv: tridiagonal eigensolver did not converge");
+          return SYK_ENUMERIC;
+        }
+        if (last || *hs >= s_rem) {
+          m_eff = mm;
+          break;
+        }
+      }
+    }
+    double s_acc = std::min(*hs, s_rem);
+    if (!(s_acc > 1e-13 * s_rem) && !(s_acc >= s_rem)) {
+      set_error("expmv: Krylov step collapsed (s=%g of remaining %g); raise krylov_dim or tol", s_acc, s_rem);
+      return SYK_ENUMERIC;
+    }
+    k_tridiag_coef<<<int(B), 64, 0, st>>>(m_eff, int(B), ws.theta, ws.Q, ws.beta0, zr, zi, nullptr, s_acc, ws.c);
+    Ops<R>::combine(ws, m_eff, ws.c, out, st);
+    SYK_CUDA_CHECK(cudaGetLastError());
+    count_bases(1);
+    cur = out;
+    if (s_acc >= s_rem) s_rem = 0.0;
+    else s_rem -= s_acc;
+  }
+  if (nsteps) *nsteps = steps;
+  return SYK_OK;
+}
+
+}  // namespace
+
+int expmv_impl(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, void* out, int64_t B,
+               double tol, KrylovWS& ws, cudaStream_t st, int* nsteps) {
+  if (ws.B != B || ws.D != P.D || ws.dtype != dtype) {
+    set_error("expmv: workspace shape mismatch");
+    return SYK_EINVAL;
+  }
+  if (!(tol > 0.0)) {
+    set_error("expmv: tol must be > 0");
+    return SYK_EINVAL;
+  }
+  if (z == std::complex<double>(0.0, 0.0)) {
+    if (out != psi)
+      SYK_CUDA_CHECK(cudaMemcpyAsync(out, psi, ws.vec_bytes(), cudaMemcpyDeviceToDevice, st));
+    if (nsteps) *nsteps = 0;
+    return SYK_OK;
+  }
+  return dtype == SYK_C64 ? expmv_T<float>(P, dtype, z, psi, out, tol, ws, st, nsteps)
+                          : expmv_T<double>(P, dtype, z, psi, out, tol, ws, st, nsteps);
+}
+
+}  // namespace syk
+
+// ---------------------------------------------------------------- C ABI
+using namespace syk;
+
+extern "C" size_t syk_workspace_bytes(int N, int dtype, int krylov_dim, int64_t batch, int kind) {
+  (void)kind;
+  if (N < 4 || (N & 1) || N > 64 || !dtype_ok(dtype) || krylov_dim < 1 || krylov_dim > SYK_MAX_KRYLOV ||
+      batch < 1 || batch > 256)
+    return 0;
+  const int64_t D = int64_t(1) << (N / 2 - 1);
+  return krylov_ws_bytes(D, dtype, krylov_dim, batch);
+}
+
+extern "C" int syk_expmv(const syk_terms* terms, int parity, int dtype, double z_re, double z_im, const void* psi,
+                         void* out, int64_t batch, int krylov_dim, double tol, void* workspace, size_t ws_bytes,
+                         void* stream, int* nsteps) {
+  clear_error();
+  if (!psi || !out || batch < 1 || batch > 256 || krylov_dim < 2 || krylov_dim > SYK_MAX_KRYLOV) {
+    set_error("syk_expmv: invalid argument (batch=%lld krylov_dim=%d)", (long long)batch, krylov_dim);
+    return SYK_EINVAL;
+  }
+  if (!std::isfinite(z_re) || !std::isfinite(z_im)) {
+    set_error("syk_expmv: non-finite z");
+    return SYK_EINVAL;
+  }
+  ApplyParams P;
+  SYK_TRY(make_apply_params(terms, parity, dtype, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t need = krylov_ws_bytes(P.D, dtype, krylov_dim, batch);
+  void* base = workspace;
+  bool owned = false;
+  if (!base) {
+    cudaError_t e = cudaMallocAsync(&base, need, st);
+    if (e != cudaSuccess) {
+      set_error("syk_expmv: cannot allocate %zu bytes of workspace: %s", need, cudaGetErrorString(e));
+      return SYK_ENOMEM;
+    }
+    owned = true;
+    ws_bytes = need;
+  }
+  KrylovWS ws;
+  int rc = krylov_ws_carve(&ws, base, ws_bytes, P.D, dtype, krylov_dim, batch);
+  if (rc == SYK_OK) rc = expmv_impl(P, dtype, {z_re, z_im}, psi, out, batch, tol, ws, st, nsteps);
+  if (owned) cudaFreeAsync(base, st);
+  return rc;
+}
+
+extern "C" int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const double* beta, const double* beta0,
+                                double z_re, double z_im, double* out, void* stream) {
+  clear_error();
+  if (m < 1 || m > SYK_MAX_KRYLOV || batch < 1 || batch > 65535 || !alpha || !beta0 || !out || (m > 1 && !beta)) {
+    set_error("syk_tridiag_expm: invalid argument (m=%d batch=%lld)", m, (long long)batch);
+    return SYK_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int B = int(batch);
+  // scratch: beta padded to m rows, theta, Q, sb, status
+  const size_t nb = align_up(sizeof(double) * m * B), nq = align_up(sizeof(double) * m * m * B);
+  const size_t total = 3 * nb + nq + align_up(sizeof(double) * B) + 256;
+  char* base = nullptr;
+  SYK_CUDA_CHECK(cudaMallocAsync((void**)&base, total, st));
+  double* bpad = (double*)base;
+  double* theta = (double*)(base + nb);
+  double* Q = (double*)(base + 2 * nb);
+  double* sb = (double*)(base + 2 * nb + nq);
+  int* status = (int*)(base + 2 * nb + nq + align_up(sizeof(double) * B));
+  cudaMemsetAsync(bpad, 0, nb, st);
+  cudaMemsetAsync(status, 0, 16, st);
+  if (m > 1) cudaMemcpyAsync(bpad, beta, sizeof(double) * (m - 1) * B, cudaMemcpyDeviceToDevice, st);
+  const size_t smem = sizeof(double) * (size_t(m) * m + 2 * m + 2);
+  k_tridiag_eig<<<B, 32, smem, st>>>(m, B, alpha, bpad, nullptr, z_re, z_im, 1.0, 1.0, theta, Q, sb, status);
+  k_tridiag_coef<<<B, 64, 0, st>>>(m, B, theta, Q, beta0, z_re, z_im, nullptr, 1.0, (double2*)out);
+  cudaError_t e = cudaGetLastError();
+  int hstat = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(base, st);
+  if (e != cudaSuccess) {
+    set_error("syk_tridiag_expm: %s", cudaGetErrorString(e));
+    return SYK_ECUDA;
+  }
+  if (hstat) {
+    set_error("syk_tridiag_expm: eigensolver did not converge");
+    return SYK_ENUMERIC;
+  }
+  return SYK_OK;
+}

@@ -1,0 +1,133 @@
+// Runtime services of the library: work counters, CUDA-event timing of every
+// apply_H launch, and a pinned host staging buffer for small device reads.
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "syk_krylov.cuh"
+
+namespace syk {
+namespace {
+
+std::atomic<int64_t> g_applies{0};
+std::atomic<int64_t> g_bases{0};
+
+struct Prof {
+  std::mutex mtx;
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches = 0;
+  double total_ms = 0.0;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+Prof& prof() {
+  static Prof* p = new Prof;  // never destroyed: events may outlive static teardown
+  return *p;
+}
+thread_local cudaEvent_t t_start = nullptr;
+
+}  // namespace
+
+void count_applies(int64_t states) { g_applies += states; }
+void count_bases(int64_t n) { g_bases += n; }
+
+void prof_before_apply(cudaStream_t st) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> lk(p.mtx);
+  if (!p.on) return;
+  t_start = p.get();
+  cudaEventRecord(t_start, st);
+}
+
+void prof_after_apply(cudaStream_t st) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> lk(p.mtx);
+  if (!p.on || !t_start) return;
+  cudaEvent_t e = p.get();
+  cudaEventRecord(e, st);
+  p.pending.emplace_back(t_start, e);
+  t_start = nullptr;
+}
+
+// Accumulates every completed event pair (called after a synchronisation).
+void prof_collect() {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> lk(p.mtx);
+  size_t keep = 0;
+  for (size_t i = 0; i < p.pending.size(); ++i) {
+    auto pr = p.pending[i];
+    if (cudaEventQuery(pr.second) == cudaSuccess) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      p.total_ms += ms;
+      p.launches += 1;
+      p.pool.push_back(pr.first);
+      p.pool.push_back(pr.second);
+    } else {
+      p.pending[keep++] = pr;
+    }
+  }
+  p.pending.resize(keep);
+}
+
+void* pinned_scratch(size_t bytes) {
+  static thread_local void* buf = nullptr;
+  static thread_local size_t cap = 0;
+  if (bytes > cap) {
+    if (buf) cudaFreeHost(buf);
+    cap = std::max<size_t>(bytes, 4096);
+    if (cudaMallocHost(&buf, cap) != cudaSuccess) {
+      buf = nullptr;
+      cap = 0;
+    }
+  }
+  return buf;
+}
+
+}  // namespace syk
+
+extern "C" int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int reset) {
+  if (h_applies) *h_applies = syk::g_applies.load();
+  if (krylov_bases) *krylov_bases = syk::g_bases.load();
+  if (reset) {
+    syk::g_applies = 0;
+    syk::g_bases = 0;
+  }
+  return SYK_OK;
+}
+
+extern "C" int syk_profile_enable(int on) {
+  syk::Prof& p = syk::prof();
+  std::lock_guard<std::mutex> lk(p.mtx);
+  p.on = on != 0;
+  return SYK_OK;
+}
+
+extern "C" int syk_profile_read(int64_t* launches, double* total_ms, int reset) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    syk::set_error("syk_profile_read: %s", cudaGetErrorString(e));
+    return SYK_ECUDA;
+  }
+  syk::prof_collect();
+  syk::Prof& p = syk::prof();
+  std::lock_guard<std::mutex> lk(p.mtx);
+  if (launches) *launches = p.launches;
+  if (total_ms) *total_ms = p.total_ms;
+  if (reset) {
+    p.launches = 0;
+    p.total_ms = 0.0;
+  }
+  return SYK_OK;
+}

@@ -1,0 +1,337 @@
+// Host side of the SYK term set: Jordan-Wigner Pauli strings of every term of
+// Eq. 1, grouped by X-mask into the coefficient tables the matvec evaluates.
+//
+// Pauli algebra (Supp. Sec. I.A).  A Pauli string is i^p X^m Z^z with
+// X^m Z^z |x> = (-1)^popcount(z & x) |x ^ m>.  Majorana a on spin k = a/2:
+//   even a: (prod_{j<k} Z_j) X_k    -> m = 1<<k, z = (1<<k)-1,            p = 0
+//   odd a:  (prod_{j<k} Z_j) Y_k    -> m = 1<<k, z = ((1<<k)-1) | (1<<k), p = 1
+// (Y = i X Z), each times 1/sqrt(2).  The product of two strings is
+//   (i^p1 X^m1 Z^z1)(i^p2 X^m2 Z^z2) = i^(p1+p2+2 popcount(z1&m2)) X^(m1^m2) Z^(z1^z2).
+// So chi_i chi_j chi_k chi_l = (1/4) i^p X^m Z^z, and term T contributes
+// w_T X^m Z^z with w_T = J_T i^p / 4.
+//
+// Matvec in grouped form.  For output index x (full spin index):
+//   (H psi)[x] = sum_m c_m(x) psi[x ^ m],
+//   c_m(x) = sum_{T in m} w_T (-1)^popcount(z_T & (x^m))
+//          = sum_{T in m} w'_T (-1)^popcount(z_T & x),   w'_T = w_T (-1)^popcount(z_T & m).
+// * popcount(m) = 4 (spins a<b<c<d, one Majorana each): z_T = zeta0 ^ s_T where
+//   s_T runs over all 16 subsets of supp(m) and zeta0 = z_T & ~m is common, so
+//   c_m(x) = (-1)^popcount(zeta0 & x) * Tm[u(x)], u(x) = bits of x at supp(m),
+//   Tm[u] = sum_T w'_T (-1)^popcount(s_T & u)   (a 16-point Walsh transform).
+// * popcount(m) = 2 (spins a<b plus a third spin c carrying both Majoranas):
+//   z_T = zeta_f ^ s_T ^ e_c, so
+//   c_m(x) = (-1)^popcount(zeta_f & x) * sum_c (-1)^x_c W_c[u(x)],
+//   W_c[u] = sum_{T with spin c} w'_T (-1)^popcount(s_T & u).
+// * m = 0 (two spins c<d, both Majoranas each): z_T = e_c ^ e_d and
+//   c_0(x) = sum_{c<d} w_cd (-1)^(x_c + x_d), w_cd real.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "syk_internal.h"
+
+namespace syk {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+namespace {
+
+struct Pauli {
+  int p;
+  uint64_t m, z;
+};
+
+Pauli majorana(int a) {
+  const int k = a / 2;
+  const uint64_t below = (uint64_t(1) << k) - 1;
+  Pauli r;
+  r.m = uint64_t(1) << k;
+  r.z = below | ((a & 1) ? (uint64_t(1) << k) : 0);
+  r.p = a & 1;
+  return r;
+}
+
+Pauli mul(const Pauli& A, const Pauli& B) {
+  Pauli r;
+  r.p = (A.p + B.p + 2 * __builtin_popcountll(A.z & B.m)) & 3;
+  r.m = A.m ^ B.m;
+  r.z = A.z ^ B.z;
+  return r;
+}
+
+// bits of v at the set positions of mask, packed from the lowest position up
+uint32_t extract_bits(uint64_t v, uint64_t mask) {
+  uint32_t out = 0;
+  int o = 0;
+  for (int k = 0; k < 64; ++k)
+    if ((mask >> k) & 1) out |= uint32_t((v >> k) & 1) << (o++);
+  return out;
+}
+
+std::complex<double> ipow(int p) {
+  static const std::complex<double> t[4] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+  return t[p & 3];
+}
+
+}  // namespace
+}  // namespace syk
+
+using syk::set_error;
+
+extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
+  syk::clear_error();
+  if (!out || !J) {
+    set_error("syk_build_terms: NULL argument");
+    return SYK_EINVAL;
+  }
+  *out = nullptr;
+  if (N < 4 || (N & 1) || N > 64) {
+    set_error("syk_build_terms: N=%d must be even, 4 <= N <= 64", N);
+    return SYK_EINVAL;
+  }
+  syk_terms* t = new (std::nothrow) syk_terms;
+  if (!t) {
+    set_error("syk_build_terms: out of host memory");
+    return SYK_ENOMEM;
+  }
+  try {
+    const int n = N / 2;
+    t->N = N;
+    t->n = n;
+    t->D = int64_t(1) << (n - 1);
+    const int64_t nt = int64_t(N) * (N - 1) * (N - 2) * (N - 3) / 24;
+    t->nterms = nt;
+    t->xm.resize(nt);
+    t->zm.resize(nt);
+    t->ph.resize(nt);
+    t->J.assign(J, J + nt);
+
+    // Pauli string of every term; group term indices by X-mask.
+    std::map<uint64_t, std::vector<int64_t>> groups;
+    std::vector<int> dbl(nt, -1);  // popcount-2 terms: the spin carrying two Majoranas
+    int64_t idx = 0;
+    for (int a = 0; a < N; ++a)
+      for (int b = a + 1; b < N; ++b)
+        for (int c = b + 1; c < N; ++c)
+          for (int d = c + 1; d < N; ++d, ++idx) {
+            using namespace syk;
+            Pauli P = mul(mul(mul(majorana(a), majorana(b)), majorana(c)), majorana(d));
+            t->xm[idx] = P.m;
+            t->zm[idx] = P.z;
+            t->ph[idx] = uint8_t(P.p);
+            const int sa = a / 2, sb = b / 2, sc = c / 2, sd = d / 2;
+            if (sa == sb) dbl[idx] = sa;
+            else if (sb == sc) dbl[idx] = sb;
+            else if (sc == sd) dbl[idx] = sc;
+            groups[P.m].push_back(idx);
+          }
+    const uint64_t Dmask = uint64_t(t->D) - 1;
+    t->wdiag.assign(size_t(n) * n, 0.0);
+    for (auto& kv : groups) {
+      const uint64_t m = kv.first;
+      const auto& terms = kv.second;
+      const int pc = __builtin_popcountll(m);
+      if (pc == 0) {
+        for (int64_t T : terms) {
+          const uint64_t z = t->zm[T];
+          if (__builtin_popcountll(z) != 2) throw std::runtime_error("diagonal term z is not e_c^e_d");
+          std::complex<double> w = t->J[T] * syk::ipow(t->ph[T]) / 4.0;
+          if (std::abs(w.imag()) > 1e-300 && std::abs(w.imag()) > 1e-15 * std::abs(w.real()))
+            throw std::runtime_error("diagonal coefficient is not real");
+          const int c = __builtin_ctzll(z), d = 63 - __builtin_clzll(z);
+          t->wdiag[size_t(c) * n + d] += w.real();
+        }
+      } else if (pc == 4) {
+        std::complex<double> tab[16];
+        const uint64_t zeta0 = t->zm[terms[0]] & ~m;
+        for (int64_t T : terms) {
+          const uint64_t z = t->zm[T];
+          if ((z & ~m) != zeta0) throw std::runtime_error("popcount-4 group: zeta0 differs");
+          const uint32_t s = syk::extract_bits(z, m);
+          std::complex<double> w = t->J[T] * syk::ipow(t->ph[T]) / 4.0;
+          if (__builtin_popcountll(z & m) & 1) w = -w;
+          for (int u = 0; u < 16; ++u) tab[u] += (__builtin_popcount(s & u) & 1) ? -w : w;
+        }
+        uint32_t supp = 0;
+        int o = 0;
+        for (int k = 0; k < n; ++k)
+          if ((m >> k) & 1) supp |= uint32_t(k) << (8 * (o++));
+        t->m4_rec.push_back(uint32_t(m & Dmask));
+        t->m4_rec.push_back(uint32_t(zeta0));
+        t->m4_rec.push_back(supp);
+        t->m4_rec.push_back(0u);
+        for (int u = 0; u < 32; ++u) {
+          std::complex<double> v = u < 16 ? tab[u] : -tab[u - 16];
+          t->m4_tab.push_back(v.real());
+          t->m4_tab.push_back(v.imag());
+        }
+        t->n4++;
+      } else if (pc == 2) {
+        std::vector<std::complex<double>> W(size_t(n) * 4);
+        uint64_t zetaf = 0;
+        bool first = true;
+        for (int64_t T : terms) {
+          const int c = dbl[T];
+          if (c < 0) throw std::runtime_error("popcount-2 term without a doubled spin");
+          const uint64_t z = t->zm[T];
+          const uint64_t r = z ^ (uint64_t(1) << c);
+          if (first) {
+            zetaf = r & ~m;
+            first = false;
+          } else if ((r & ~m) != zetaf) {
+            throw std::runtime_error("popcount-2 group: zeta_f differs");
+          }
+          const uint32_t s = syk::extract_bits(r, m);
+          std::complex<double> w = t->J[T] * syk::ipow(t->ph[T]) / 4.0;
+          if (__builtin_popcountll(z & m) & 1) w = -w;
+          for (int u = 0; u < 4; ++u) W[size_t(c) * 4 + u] += (__builtin_popcount(s & u) & 1) ? -w : w;
+        }
+        const int a = __builtin_ctzll(m), b = 63 - __builtin_clzll(m);
+        t->m2_rec.push_back(uint32_t(m & Dmask));
+        t->m2_rec.push_back(uint32_t(zetaf));
+        t->m2_rec.push_back(uint32_t(a) | (uint32_t(b) << 8));
+        t->m2_rec.push_back(0u);
+        for (auto& v : W) {
+          t->m2_tab.push_back(v.real());
+          t->m2_tab.push_back(v.imag());
+        }
+        t->n2++;
+      } else {
+        throw std::runtime_error("X-mask with odd popcount or popcount > 4");
+      }
+    }
+    for (double v : t->J)
+      if (!std::isfinite(v)) throw std::runtime_error("non-finite coupling");
+  } catch (const std::bad_alloc&) {
+    delete t;
+    set_error("syk_build_terms: out of host memory");
+    return SYK_ENOMEM;
+  } catch (const std::exception& e) {
+    delete t;
+    set_error("syk_build_terms: %s", e.what());
+    return SYK_EINVAL;
+  }
+  *out = t;
+  return SYK_OK;
+}
+
+extern "C" void syk_free_terms(syk_terms* t) {
+  if (!t) return;
+  if (t->dev.device >= 0) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(t->dev.device);
+    void* ptrs[] = {t->dev.m4_rec, t->dev.m4_t64, t->dev.m4_t32, t->dev.m2_rec,
+                    t->dev.m2_t64, t->dev.m2_t32, t->dev.wd64,  t->dev.wd32};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  delete t;
+}
+
+extern "C" int syk_terms_info(const syk_terms* t, int* N, int64_t* nterms, int64_t* nmasks,
+                              int64_t* dim) {
+  if (!t) {
+    set_error("syk_terms_info: NULL terms");
+    return SYK_EINVAL;
+  }
+  if (N) *N = t->N;
+  if (nterms) *nterms = t->nterms;
+  if (nmasks) *nmasks = int64_t(t->n4) + t->n2 + 1;
+  if (dim) *dim = t->D;
+  return SYK_OK;
+}
+
+extern "C" int syk_term_table(const syk_terms* t, uint64_t* xmask, uint64_t* zmask, uint8_t* phase) {
+  if (!t) {
+    set_error("syk_term_table: NULL terms");
+    return SYK_EINVAL;
+  }
+  if (xmask) std::memcpy(xmask, t->xm.data(), t->xm.size() * sizeof(uint64_t));
+  if (zmask) std::memcpy(zmask, t->zm.data(), t->zm.size() * sizeof(uint64_t));
+  if (phase) std::memcpy(phase, t->ph.data(), t->ph.size());
+  return SYK_OK;
+}
+
+extern "C" const char* syk_last_error(void) { return syk::g_err.c_str(); }
+
+namespace syk {
+
+template <typename T>
+static int upload(T** dst, const void* src, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  SYK_CUDA_CHECK(cudaMalloc((void**)dst, bytes));
+  if (src) SYK_CUDA_CHECK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  return SYK_OK;
+}
+
+int ensure_device_tables(const syk_terms* t) {
+  int cur = -1;
+  SYK_CUDA_CHECK(cudaGetDevice(&cur));
+  std::lock_guard<std::mutex> lock(t->mtx);
+  if (t->dev.device == cur) return SYK_OK;
+  if (t->dev.device >= 0) {
+    set_error("term tables were uploaded to device %d; current device is %d", t->dev.device, cur);
+    return SYK_EINVAL;
+  }
+  DeviceTables& d = t->dev;
+  std::vector<float> f4(t->m4_tab.begin(), t->m4_tab.end());
+  std::vector<float> f2(t->m2_tab.begin(), t->m2_tab.end());
+  std::vector<float> fd(t->wdiag.begin(), t->wdiag.end());
+  SYK_TRY(upload(&d.m4_rec, t->m4_rec.data(), t->m4_rec.size() * 4));
+  SYK_TRY(upload(&d.m4_t64, t->m4_tab.data(), t->m4_tab.size() * 8));
+  SYK_TRY(upload(&d.m4_t32, f4.data(), f4.size() * 4));
+  SYK_TRY(upload(&d.m2_rec, t->m2_rec.data(), t->m2_rec.size() * 4));
+  SYK_TRY(upload(&d.m2_t64, t->m2_tab.data(), t->m2_tab.size() * 8));
+  SYK_TRY(upload(&d.m2_t32, f2.data(), f2.size() * 4));
+  SYK_TRY(upload(&d.wd64, t->wdiag.data(), t->wdiag.size() * 8));
+  SYK_TRY(upload(&d.wd32, fd.data(), fd.size() * 4));
+  d.device = cur;
+  return SYK_OK;
+}
+
+int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p) {
+  if (!t || !p) {
+    set_error("NULL terms");
+    return SYK_EINVAL;
+  }
+  if (parity != 0 && parity != 1) {
+    set_error("parity must be 0 or 1 (got %d)", parity);
+    return SYK_EINVAL;
+  }
+  if (!dtype_ok(dtype)) {
+    set_error("dtype must be SYK_C64 or SYK_C128 (got %d)", dtype);
+    return SYK_EINVAL;
+  }
+  SYK_TRY(ensure_device_tables(t));
+  p->n = t->n;
+  p->sector = parity;
+  p->D = t->D;
+  p->n4 = t->n4;
+  p->n2 = t->n2;
+  p->m4_rec = t->dev.m4_rec;
+  p->m2_rec = t->dev.m2_rec;
+  const bool f = dtype == SYK_C64;
+  p->m4_tab = f ? (const void*)t->dev.m4_t32 : (const void*)t->dev.m4_t64;
+  p->m2_tab = f ? (const void*)t->dev.m2_t32 : (const void*)t->dev.m2_t64;
+  p->wd = f ? (const void*)t->dev.wd32 : (const void*)t->dev.wd64;
+  return SYK_OK;
+}
+
+}  // namespace syk

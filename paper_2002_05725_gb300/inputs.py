@@ -62,3 +62,20 @@ def random_tridiagonal(m: int, seed: int = 0, scale: float = 1.0):
     alpha = rng.normal(0.0, scale, size=m)
     beta = np.abs(rng.normal(0.0, scale, size=max(m - 1, 0))) + 0.05 * scale
     return alpha, beta
+
+
+def random_states_device(N: int, nstates: int, seed: int, device, dtype):
+    """(D, nstates) Gaussian random states drawn directly in device memory.
+
+    For sizes where a host draw is too slow (N >= 48).  Seeded by a torch
+    generator on ``device``; real and imaginary parts are standard normal.
+    """
+    import torch
+    D = sector_dim(N)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    real = torch.float32 if dtype == torch.complex64 else torch.float64
+    out = torch.empty((D, nstates), dtype=dtype, device=device)
+    v = torch.view_as_real(out)
+    v.copy_(torch.randn(v.shape, generator=g, device=device, dtype=real))
+    return out

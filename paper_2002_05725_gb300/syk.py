@@ -1,0 +1,250 @@
+"""Python binding of the libsyk_gb300 C ABI (include/syk.h): argument marshalling only.
+
+Functions carry the C names.  Device vectors are torch CUDA tensors of shape
+(D, B) (compact sector index x batch column, row-major = state-interleaved)
+with dtype complex64 (SYK_C64) or complex128 (SYK_C128).  Every computation
+runs in the CUDA library; if it is not built, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SYK_OK = 0
+SYK_C64 = 1
+SYK_C128 = 2
+MAX_KRYLOV = 64
+
+
+class SykError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads the shared library (building it first only if asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise SykError(f"CUDA library {_build.LIB} is not built; run __graft_entry__.build() "
+                           "or python -m paper_2002_05725_gb300.build")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, i32, dbl, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "syk_build_terms": (i32, [i32, vp, ctypes.POINTER(vp)]),
+        "syk_free_terms": (None, [vp]),
+        "syk_terms_info": (i32, [vp, vp, vp, vp, vp]),
+        "syk_term_table": (i32, [vp, vp, vp, vp]),
+        "syk_apply_H": (i32, [vp, i32, i32, vp, vp, i64, vp]),
+        "syk_apply_chi": (i32, [i32, i32, i32, i32, vp, vp, i64, vp]),
+        "syk_tridiag_expm": (i32, [i32, i64, vp, vp, vp, dbl, dbl, vp, vp]),
+        "syk_workspace_bytes": (sz, [i32, i32, i32, i64, i32]),
+        "syk_expmv": (i32, [vp, i32, i32, dbl, dbl, vp, vp, i64, i32, dbl, vp, sz, vp, vp]),
+        "syk_correlator_G": (i32, [vp, dbl, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp, vp]),
+        "syk_otoc": (i32, [vp, dbl, i32, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp]),
+        "syk_last_error": (ctypes.c_char_p, []),
+        "syk_counters": (i32, [vp, vp, i32]),
+        "syk_profile_enable": (i32, [i32]),
+        "syk_profile_read": (i32, [vp, vp, i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names declared in include/syk.h that the loaded library must export."""
+    return ["syk_build_terms", "syk_free_terms", "syk_terms_info", "syk_term_table", "syk_apply_H",
+            "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_correlator_G",
+            "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read"]
+
+
+def _check(rc: int, what: str):
+    if rc != SYK_OK:
+        msg = load().syk_last_error().decode(errors="replace")
+        raise SykError(f"{what} failed with code {rc}: {msg}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return SYK_C64
+    if t.dtype == torch.complex128:
+        return SYK_C128
+    raise SykError(f"unsupported dtype {t.dtype}")
+
+
+def _as_cols(t):
+    if t.dim() == 1:
+        return t.reshape(-1, 1)
+    if t.dim() != 2:
+        raise SykError("vectors must have shape (D,) or (D, B)")
+    return t
+
+
+class Terms:
+    """Owns a syk_terms* (freed with syk_free_terms)."""
+
+    def __init__(self, ptr: int, N: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.N = N
+        info = syk_terms_info(self)
+        self.nterms, self.nmasks, self.D = info["nterms"], info["nmasks"], info["dim"]
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.syk_free_terms(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+
+def syk_build_terms(N: int, J) -> Terms:
+    L = load()
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(L.syk_build_terms(int(N), J.ctypes.data, ctypes.byref(out)), "syk_build_terms")
+    return Terms(out.value, int(N))
+
+
+def syk_terms_info(terms: Terms) -> dict:
+    N = ctypes.c_int()
+    nt, nm, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().syk_terms_info(terms.ptr, ctypes.byref(N), ctypes.byref(nt), ctypes.byref(nm), ctypes.byref(d)),
+           "syk_terms_info")
+    return {"N": N.value, "nterms": nt.value, "nmasks": nm.value, "dim": d.value}
+
+
+def syk_term_table(terms: Terms):
+    xm = np.zeros(terms.nterms, dtype=np.uint64)
+    zm = np.zeros(terms.nterms, dtype=np.uint64)
+    ph = np.zeros(terms.nterms, dtype=np.uint8)
+    _check(load().syk_term_table(terms.ptr, xm.ctypes.data, zm.ctypes.data, ph.ctypes.data), "syk_term_table")
+    return xm, zm, ph
+
+
+def syk_apply_H(terms: Terms, parity: int, psi, out=None, stream=None):
+    import torch
+    p = _as_cols(psi)
+    y = torch.empty_like(p) if out is None else _as_cols(out)
+    _check(load().syk_apply_H(terms.ptr, int(parity), _dtype_code(p), p.data_ptr(), y.data_ptr(), p.shape[1],
+                              _stream(stream)), "syk_apply_H")
+    return y.reshape(psi.shape)
+
+
+def syk_apply_chi(N: int, i: int, parity_in: int, psi, out=None, stream=None):
+    import torch
+    p = _as_cols(psi)
+    y = torch.empty_like(p) if out is None else _as_cols(out)
+    _check(load().syk_apply_chi(int(N), int(i), int(parity_in), _dtype_code(p), p.data_ptr(), y.data_ptr(),
+                                p.shape[1], _stream(stream)), "syk_apply_chi")
+    return y.reshape(psi.shape)
+
+
+def syk_tridiag_expm(alpha, beta, beta0, z: complex, stream=None):
+    """alpha (m, B), beta (m-1, B), beta0 (B,) float64 CUDA tensors -> (m, B) complex128."""
+    import torch
+    m, B = alpha.shape
+    out = torch.empty((m, B), dtype=torch.complex128, device=alpha.device)
+    bptr = beta.data_ptr() if beta.numel() else alpha.data_ptr()
+    _check(load().syk_tridiag_expm(m, B, alpha.data_ptr(), bptr, beta0.data_ptr(), float(z.real), float(z.imag),
+                                   out.data_ptr(), _stream(stream)), "syk_tridiag_expm")
+    return out
+
+
+def syk_workspace_bytes(N: int, dtype: int, krylov_dim: int, batch: int, kind: int = 0) -> int:
+    return int(load().syk_workspace_bytes(int(N), int(dtype), int(krylov_dim), int(batch), int(kind)))
+
+
+def syk_expmv(terms: Terms, parity: int, z: complex, psi, krylov_dim: int = 40, tol: float = 1e-12, out=None,
+              workspace=None, stream=None):
+    """Returns (e^{zH} psi, number of Krylov bases)."""
+    import torch
+    p = _as_cols(psi)
+    y = torch.empty_like(p) if out is None else _as_cols(out)
+    ns = ctypes.c_int(0)
+    wptr, wbytes = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (None, 0)
+    z = complex(z)
+    _check(load().syk_expmv(terms.ptr, int(parity), _dtype_code(p), z.real, z.imag, p.data_ptr(), y.data_ptr(),
+                            p.shape[1], int(krylov_dim), float(tol), wptr, wbytes, _stream(stream),
+                            ctypes.byref(ns)), "syk_expmv")
+    return y.reshape(psi.shape), ns.value
+
+
+def _input_ptr(psi0):
+    """(pointer, B, dtype code, keep-alive) for a CUDA tensor, a host tensor or a numpy array."""
+    if isinstance(psi0, np.ndarray):
+        a = np.ascontiguousarray(psi0)
+        a2 = a.reshape(a.shape[0], -1)
+        code = SYK_C64 if a.dtype == np.complex64 else SYK_C128 if a.dtype == np.complex128 else None
+        if code is None:
+            raise SykError("numpy input must be complex64 or complex128")
+        return a.ctypes.data, a2.shape[1], code, a
+    t = _as_cols(psi0)
+    if not t.is_contiguous():
+        raise SykError("input tensor must be contiguous")
+    return t.data_ptr(), t.shape[1], _dtype_code(t), t
+
+
+def syk_correlator_G(terms: Terms, beta: float, i: int, times, psi0, krylov_dim: int = 30, tol: float = 1e-12,
+                     stream=None):
+    """Returns (G complex (nt, B), Z (B,)) for G(t) = <phi|chi_i(t) chi_i|phi>/<phi|phi>."""
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    ptr, B, code, keep = _input_ptr(psi0)
+    G = np.zeros((len(t), B, 2))
+    Z = np.zeros(B)
+    _check(load().syk_correlator_G(terms.ptr, float(beta), int(i), t.ctypes.data, len(t), ptr, B, code,
+                                   int(krylov_dim), float(tol), G.ctypes.data, Z.ctypes.data, _stream(stream)),
+           "syk_correlator_G")
+    del keep
+    return G[..., 0] + 1j * G[..., 1], Z
+
+
+def syk_otoc(terms: Terms, beta: float, i: int, j: int, times, psi0, krylov_dim: int = 40, tol: float = 1e-12,
+             stream=None):
+    """Returns the unnormalised regularized OTOC F (nt, B) complex; F~ = F / F[t=0]."""
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    ptr, B, code, keep = _input_ptr(psi0)
+    F = np.zeros((len(t), B, 2))
+    _check(load().syk_otoc(terms.ptr, float(beta), int(i), int(j), t.ctypes.data, len(t), ptr, B, code,
+                           int(krylov_dim), float(tol), F.ctypes.data, _stream(stream)), "syk_otoc")
+    del keep
+    return F[..., 0] + 1j * F[..., 1]
+
+
+def syk_counters(reset: bool = False):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().syk_counters(ctypes.byref(a), ctypes.byref(b), int(reset)), "syk_counters")
+    return {"h_applies": a.value, "krylov_bases": b.value}
+
+
+def syk_profile_enable(on: bool = True):
+    _check(load().syk_profile_enable(int(on)), "syk_profile_enable")
+
+
+def syk_profile_read(reset: bool = False):
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(load().syk_profile_read(ctypes.byref(n), ctypes.byref(ms), int(reset)), "syk_profile_read")
+    return {"launches": n.value, "total_ms": ms.value}

@@ -1,0 +1,117 @@
+"""K1 (apply_H) and K5 (apply_chi) on the GPU against the CPU oracle."""
+import numpy as np
+import pytest
+
+from helpers import TOL, rel, tdtype, to_dev, torch_or_skip
+from oracle import hamiltonian as hm
+from paper_2002_05725_gb300 import inputs, syk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = torch_or_skip()
+    syk.load(build_if_missing=True)
+    return t
+
+
+@pytest.mark.parametrize("N", [4, 8, 12, 16, 20])
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_H_vs_oracle_full(torch, N, dt):
+    J = inputs.couplings(N, 21)
+    terms = syk.syk_build_terms(N, J)
+    for sector in (0, 1):
+        H = hm.H_sector_sparse(N, J, sector)
+        for B in (1, 3, 19):
+            psi = inputs.random_states(N, B, 100 + B)
+            ref = H @ psi.T
+            y = syk.syk_apply_H(terms, sector, to_dev(torch, psi, dt))
+            assert rel(y.cpu().numpy(), ref) < TOL[dt], (N, sector, B)
+
+
+@pytest.mark.parametrize("N", [28, 32, 40])
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_H_sampled_rows(torch, N, dt):
+    """Brute force over all C(N,4) terms on sampled rows (first, last, random)."""
+    J = inputs.couplings(N, 5)
+    terms = syk.syk_build_terms(N, J)
+    D = 1 << (N // 2 - 1)
+    psi = inputs.random_states(N, 2, 7)
+    rng = np.random.default_rng(N)
+    rows = np.unique(np.concatenate([[0, 1, D - 1], rng.integers(0, D, 21)]))
+    for sector in (0, 1):
+        y = syk.syk_apply_H(terms, sector, to_dev(torch, psi, dt)).cpu().numpy()
+        ref = hm.apply_rows(N, J, sector, psi.T, rows)
+        assert rel(y[rows], ref) < TOL[dt], (N, sector)
+
+
+def test_apply_H_sampled_rows_N60(torch):
+    """N = 60, even sector of dimension 2^29, complex64 (4 GiB per vector)."""
+    N = 60
+    J = inputs.couplings(N, 1)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states_device(N, 1, 60, "cuda", torch.complex64)
+    y = syk.syk_apply_H(terms, 0, psi)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(60)
+    D = 1 << (N // 2 - 1)
+    rows = np.concatenate([[0, D - 1], rng.integers(0, D, 6)])
+    m = hm.flip_mask(hm.quadruples(N))
+    ys = y[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    for r, c in enumerate(rows):
+        x = int(hm.full_index(N, 0, c))
+        src = np.unique((np.int64(x) ^ m) & (D - 1))
+        vals = psi[torch.as_tensor(src, device="cuda"), 0].cpu().numpy().astype(np.complex128)
+        full = np.zeros(1, dtype=np.complex128)
+        # oracle row over all terms, reading psi only at the sources it gathers
+        lookup = dict(zip(src.tolist(), vals.tolist()))
+        srcs = (np.int64(x) ^ m) & (D - 1)
+        amp, xo = hm.term_action(hm.quadruples(N), np.int64(x) ^ m)
+        assert np.all(xo == x)
+        full[0] = np.sum(J * amp * np.array([lookup[s] for s in srcs.tolist()]))
+        assert abs(ys[r, 0] - full[0]) < 4e-5 * max(1.0, abs(full[0])), (r, ys[r, 0], full[0])
+
+
+def test_apply_H_hermitian(torch):
+    N = 32
+    J = inputs.couplings(N, 9)
+    terms = syk.syk_build_terms(N, J)
+    a = to_dev(torch, inputs.random_states(N, 3, 1), "c128")
+    b = to_dev(torch, inputs.random_states(N, 3, 2), "c128")
+    Ha = syk.syk_apply_H(terms, 0, a)
+    Hb = syk.syk_apply_H(terms, 0, b)
+    lhs = (a.conj() * Hb).sum(0)
+    rhs = (Ha.conj() * b).sum(0)
+    assert torch.max(torch.abs(lhs - rhs)).item() < 1e-11 * torch.max(torch.abs(lhs)).item()
+    # <psi|H^2|psi>/<psi|psi> = sum J^2/16 up to the typicality error ~ D^{-1/2}
+    e2 = (Ha.abs() ** 2).sum(0) / (a.abs() ** 2).sum(0)
+    assert np.allclose(e2.cpu().numpy(), np.sum(J ** 2) / 16, rtol=0.05)
+
+
+@pytest.mark.parametrize("N", [4, 12, 20])
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_chi_vs_oracle(torch, N, dt):
+    psi = inputs.random_states(N, 3, 4)
+    for sector in (0, 1):
+        for i in range(N):
+            ref = hm.chi_sector_sparse(N, i, sector) @ psi.T
+            y = syk.syk_apply_chi(N, i, sector, to_dev(torch, psi, dt))
+            assert rel(y.cpu().numpy(), ref) < (1e-15 if dt == "c128" else 1e-7), (i, sector)
+
+
+def test_apply_chi_squares_to_half(torch):
+    N = 36
+    psi = inputs.random_states_device(N, 2, 3, "cuda", torch.complex128)
+    for i in (0, 17, 35):
+        y = syk.syk_apply_chi(N, i, 1, syk.syk_apply_chi(N, i, 0, psi))
+        assert torch.max(torch.abs(y - psi / 2)).item() < 1e-15
+
+
+def test_apply_H_invalid_args(torch):
+    terms = syk.syk_build_terms(8, inputs.couplings(8, 0))
+    psi = torch.zeros((8, 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(syk.SykError):
+        syk.syk_apply_H(terms, 2, psi)
+    with pytest.raises(syk.SykError):
+        syk.syk_apply_H(terms, 0, psi[:, :0])
