@@ -1,15 +1,31 @@
 // K1: y = H psi in one parity sector, matrix-free (Supp. Sec. I.B), and
 // K5: y = chi_i psi (Supp. Sec. I.A).
 //
-// One thread owns one output row x (compact index) and BT batch columns.  It
-// evaluates every X-mask coefficient c_m(x) from the grouped tables built on
-// the host (see syk_terms.cpp) and gathers psi[x ^ m] for the BT columns:
+// Every output row x (compact index) sums over all X-masks, with each mask
+// coefficient c_m(x) evaluated on the fly from the grouped tables built on the
+// host (see syk_terms.cpp):
 //   y[x][b] = c_0(x) psi[x][b] + sum_{popcount(m)=2} c_m(x) psi[x^m][b]
 //                              + sum_{popcount(m)=4} c_m(x) psi[x^m][b].
 // The full spin index of x (needed for the sign parities) is
 //   xf = x | ((popcount(x) + sector) & 1) << (n-1);
 // the gather index is x ^ (m & (D-1)) because every X-mask has even popcount.
+//
+// k_apply_tiled (main path, batch of 1, 2, 4, 8 or 16 columns): a CTA owns a
+// tile of T = 256 * RPT consecutive rows.  Masks are walked in groups sharing
+// the compact-mask bits above the tile, so each group reads ONE partner tile
+// psi[tile ^ h]; that tile (T * BT contiguous elements) is staged in shared
+// memory by a bulk asynchronous copy (cp.async.bulk + mbarrier), double
+// buffered so the next group's tile streams in during the current group's
+// arithmetic.  A thread owns RPT rows that differ in compact bits 8, 9, 10; the
+// table index of a popcount-4 mask for those rows follows from the first row's
+// by XOR with per-mask flip patterns, so the bit extraction is done once per
+// mask.  Rows wider than 16 bytes are read in 16-byte chunks in a lane-rotated
+// order so that the 32 lanes of a warp hit distinct shared-memory banks.
+// k_apply_rows (fallback: any batch, any alignment, small sectors): one thread
+// per row, gathers straight from global memory.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include <algorithm>
 #include <vector>
@@ -21,7 +37,7 @@ namespace syk {
 namespace {
 
 template <typename R, int BT>
-__global__ void __launch_bounds__(128) k_apply_H(ApplyParams p, const typename CT<R>::T* __restrict__ psi,
+__global__ void __launch_bounds__(128) k_apply_rows(ApplyParams p, const typename CT<R>::T* __restrict__ psi,
                                                  typename CT<R>::T* __restrict__ y, int64_t ld, int64_t b0) {
   using C = typename CT<R>::T;
   const C* __restrict__ t4 = static_cast<const C*>(p.m4_tab);
@@ -100,11 +116,16 @@ void launch_one(const ApplyParams& p, const void* psi, void* y, int64_t ld, int6
   const int threads = 128;
   int64_t blocks = (p.D + threads - 1) / threads;
   blocks = std::min<int64_t>(blocks, 152 * 64);
-  k_apply_H<R, BT><<<(unsigned)blocks, threads, 0, st>>>(p, static_cast<const C*>(psi), static_cast<C*>(y), ld, b0);
+  k_apply_rows<R, BT><<<(unsigned)blocks, threads, 0, st>>>(p, static_cast<const C*>(psi), static_cast<C*>(y), ld, b0);
 }
 
 template <typename R>
+int try_tiled(const ApplyParams& p, const void* psi, void* y, int64_t batch, cudaStream_t st);
+
+template <typename R>
 int launch_apply_T(const ApplyParams& p, const void* psi, void* y, int64_t batch, cudaStream_t st) {
+  const int rc = try_tiled<R>(p, psi, y, batch, st);
+  if (rc <= 0) return rc;  // launched (0) or failed (< 0)
   int64_t b0 = 0;
   while (b0 < batch) {
     const int64_t rem = batch - b0;
@@ -116,6 +137,296 @@ int launch_apply_T(const ApplyParams& p, const void* psi, void* y, int64_t batch
   }
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
+}
+
+// ---------------------------------------------------------------- tiled matvec
+namespace tma {
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+// bulk global -> shared copy; completion is signalled on mbarrier b as transaction bytes
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(b))
+               : "memory");
+}
+__device__ __forceinline__ bool try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of b; gives up after a bounded number of polls.
+__device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (try_wait(b, parity)) return true;
+  return false;
+}
+}  // namespace tma
+
+template <typename R>
+struct Slot;  // 16-byte chunk of a row
+template <>
+struct Slot<float> {
+  using T = float4;  // two complex64
+  static __device__ __forceinline__ void mac(float4& a, float cr, float ci, const float4 v) {
+    a.x = fmaf(cr, v.x, fmaf(-ci, v.y, a.x));
+    a.y = fmaf(cr, v.y, fmaf(ci, v.x, a.y));
+    a.z = fmaf(cr, v.z, fmaf(-ci, v.w, a.z));
+    a.w = fmaf(cr, v.w, fmaf(ci, v.z, a.w));
+  }
+  static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct Slot<double> {
+  using T = double2;  // one complex128
+  static __device__ __forceinline__ void mac(double2& a, double cr, double ci, const double2 v) { cmac(a, cr, ci, v); }
+  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+};
+
+// diagonal coefficient c_0(x) = sum_{c<d} w_cd (-1)^{x_c + x_d}
+template <typename R>
+__device__ __forceinline__ R diag_coef(const R* __restrict__ wd, int n, uint32_t xf) {
+  R dsum = R(0);
+  for (int c = 0; c < n - 1; ++c) {
+    R inner = R(0);
+    for (int d = c + 1; d < n; ++d) {
+      const R w = __ldg(&wd[c * n + d]);
+      inner += ((xf >> d) & 1u) ? -w : w;
+    }
+    dsum += ((xf >> c) & 1u) ? -inner : inner;
+  }
+  return dsum;
+}
+
+// popcount-2 coefficient c_m(x) = (-1)^{popcount(zeta_f & x)} sum_c (-1)^{x_c} W_c[u(x)]
+template <typename C, typename R>
+__device__ __forceinline__ void pc2_coef(const C* __restrict__ t2, int k, int n, uint4 rec, uint32_t xf, R& cr,
+                                         R& ci) {
+  const uint32_t a = rec.z & 0xffu, bb = (rec.z >> 8) & 0xffu;
+  const uint32_t u = ((xf >> a) & 1u) | (((xf >> bb) & 1u) << 1);
+  const C* W = t2 + (size_t)k * n * 4 + u;
+  cr = R(0);
+  ci = R(0);
+  for (int c = 0; c < n; ++c) {
+    const C w = __ldg(&W[4 * c]);
+    if ((xf >> c) & 1u) {
+      cr -= w.x;
+      ci -= w.y;
+    } else {
+      cr += w.x;
+      ci += w.y;
+    }
+  }
+  if (__popc(rec.y & xf) & 1) {
+    cr = -cr;
+    ci = -ci;
+  }
+}
+
+template <typename R, int BT, int RPT>
+struct TileCfg {
+  using C = typename CT<R>::T;
+  static constexpr int NT = 256;
+  static constexpr int T = NT * RPT;  // rows per tile
+  static constexpr int ROWB = BT * (int)sizeof(C);
+  static constexpr int TILEB = T * ROWB;
+  static constexpr int CH = ROWB >= 16 ? ROWB / 16 : 0;  // 16-byte chunks per row
+  static constexpr int NS = CH ? CH : 1;
+  static constexpr size_t SMEM = 2 * (size_t)TILEB + 64;
+};
+
+template <typename R, int BT, int RPT>
+__global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* __restrict__ groups, int ngroups,
+                                                     const typename CT<R>::T* __restrict__ psi,
+                                                     typename CT<R>::T* __restrict__ y) {
+  using Cfg = TileCfg<R, BT, RPT>;
+  using C = typename CT<R>::T;
+  using S = typename std::conditional<Cfg::CH == 0, C, typename Slot<R>::T>::type;
+  constexpr int NT = Cfg::NT, T = Cfg::T, ROWB = Cfg::ROWB, TILEB = Cfg::TILEB, CH = Cfg::CH, NS = Cfg::NS;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * TILEB);
+  const C* __restrict__ t4 = static_cast<const C*>(p.m4_tab);
+  const C* __restrict__ t2 = static_cast<const C*>(p.m2_tab);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t tile = blockIdx.x;
+  const int n = p.n;
+  const int rho = CH >= 8 ? (lane & 7) : (CH >= 2 ? ((lane * CH / 8) % CH) : 0);
+  uint32_t xf[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const uint32_t xc = tile * (uint32_t)T + (uint32_t)(tid + i * NT);
+    xf[i] = xc | ((uint32_t)((__popc(xc) + p.sector) & 1) << (n - 1));
+  }
+  S acc[RPT][NS];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if constexpr (CH == 0) acc[i][k] = make_c<R>(R(0), R(0));
+      else acc[i][k] = Slot<R>::zero();
+    }
+
+  // y_row += (cr + i ci) * psi_tile[sr] for this thread's row slot i
+  auto mac_row = [&](S* a, R cr, R ci, const unsigned char* tb, uint32_t sr) {
+    if constexpr (CH == 0) {
+      const C v = reinterpret_cast<const C*>(tb)[sr];
+      cmac(a[0], cr, ci, v);
+    } else {
+      const S* row = reinterpret_cast<const S*>(tb + (size_t)sr * ROWB);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) Slot<R>::mac(a[k], cr, ci, row[(k + rho) & (CH - 1)]);
+    }
+  };
+
+  if (tid == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+  const unsigned char* src = reinterpret_cast<const unsigned char*>(psi);
+  auto issue = [&](int g) {
+    if (tid == 0) {
+      const int b = g & 1;
+      const uint32_t part = tile ^ (uint32_t)__ldg(&groups[g].x);
+      tma::expect_tx(&bar[b], TILEB);
+      tma::bulk_load(sm + b * TILEB, src + (size_t)part * TILEB, TILEB, &bar[b]);
+    }
+  };
+  issue(0);
+  bool failed = false;
+  int g = 0;
+  for (; g < ngroups; ++g) {
+    if (g + 1 < ngroups) issue(g + 1);
+    const bool ok = tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
+    const int4 gr = __ldg(&groups[g]);
+    const unsigned char* tb = sm + (g & 1) * TILEB;
+    if (ok) {
+      // popcount-4 masks of this group
+      for (int k = gr.y; k < gr.z; ++k) {
+        const uint4 rec = __ldg(&p.m4_rec[k]);
+        const uint32_t lo = rec.x & (uint32_t)(T - 1);
+        const uint32_t s = rec.z, x0 = xf[0];
+        const uint32_t u = ((x0 >> (s & 0xffu)) & 1u) | (((x0 >> ((s >> 8) & 0xffu)) & 1u) << 1) |
+                           (((x0 >> ((s >> 16) & 0xffu)) & 1u) << 2) | (((x0 >> (s >> 24)) & 1u) << 3);
+        const uint32_t idx0 = u | ((__popc(rec.y & x0) & 1u) << 4);
+        const C* tab = t4 + (size_t)k * 32;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          uint32_t idx = idx0;
+          if (i & 1) idx ^= rec.w & 31u;
+          if (i & 2) idx ^= (rec.w >> 5) & 31u;
+          if (i & 4) idx ^= (rec.w >> 10) & 31u;
+          const C cf = __ldg(&tab[idx]);
+          mac_row(acc[i], cf.x, cf.y, tb, (uint32_t)(tid + i * NT) ^ lo);
+        }
+      }
+      // popcount-2 masks
+      const int k2e = gr.w >> 16;
+      for (int k = gr.w & 0xffff; k < k2e; ++k) {
+        const uint4 rec = __ldg(&p.m2_rec[k]);
+        const uint32_t lo = rec.x & (uint32_t)(T - 1);
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          R cr, ci;
+          pc2_coef<C, R>(t2, k, n, rec, xf[i], cr, ci);
+          mac_row(acc[i], cr, ci, tb, (uint32_t)(tid + i * NT) ^ lo);
+        }
+      }
+      // diagonal (the own tile is the group with h = 0)
+      if (gr.x == 0) {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+          mac_row(acc[i], diag_coef<R>(static_cast<const R*>(p.wd), n, xf[i]), R(0), tb, (uint32_t)(tid + i * NT));
+      }
+    }
+    // every thread is done with buffer g&1 before it is refilled; agree on failure
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+  }
+  if (failed) {
+    // drain: let any copy still in flight land before the CTA exits
+    if (tid == 0) {
+      atomicOr(p.status, 4);
+      tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
+      if (g + 1 < ngroups) tma::wait_bounded(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
+    }
+    __syncthreads();
+    return;
+  }
+  unsigned char* dst = reinterpret_cast<unsigned char*>(y);
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const size_t row = (size_t)tile * T + (size_t)(tid + i * NT);
+    if constexpr (CH == 0) {
+      reinterpret_cast<C*>(dst)[row] = acc[i][0];
+    } else {
+      S* out = reinterpret_cast<S*>(dst + row * ROWB);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) out[(k + rho) & (CH - 1)] = acc[i][k];
+    }
+  }
+}
+
+template <typename R, int BT, int RPT>
+int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st) {
+  using Cfg = TileCfg<R, BT, RPT>;
+  using C = typename CT<R>::T;
+  int tb = 0;
+  while ((1 << tb) < Cfg::T) ++tb;
+  const int4* groups = nullptr;
+  int ng = 0;
+  SYK_TRY(tile_groups(p.terms, tb, &groups, &ng));
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Cfg::SMEM));
+    attr_set = true;
+  }
+  const unsigned blocks = (unsigned)(p.D / Cfg::T);
+  k_apply_tiled<R, BT, RPT><<<blocks, Cfg::NT, Cfg::SMEM, st>>>(p, groups, ng, static_cast<const C*>(psi),
+                                                                 static_cast<C*>(y));
+  SYK_CUDA_CHECK(cudaGetLastError());
+  return SYK_OK;
+}
+
+// Tiled path for a whole batch of 1, 2, 4, 8 or 16 columns; returns 1 if not applicable.
+template <typename R>
+int try_tiled(const ApplyParams& p, const void* psi, void* y, int64_t batch, cudaStream_t st) {
+  if ((reinterpret_cast<uintptr_t>(psi) & 15) || (reinterpret_cast<uintptr_t>(y) & 15)) return 1;
+  constexpr bool F = sizeof(R) == 4;
+  auto fits = [&](int T) { return p.D >= T; };
+  switch (batch) {
+    case 1:
+      if (!fits(F ? 2048 : 1024)) return 1;
+      return F ? launch_tiled<R, 1, 8>(p, psi, y, st) : launch_tiled<R, 1, 4>(p, psi, y, st);
+    case 2:
+      if (!fits(F ? 1024 : 512)) return 1;
+      return F ? launch_tiled<R, 2, 4>(p, psi, y, st) : launch_tiled<R, 2, 2>(p, psi, y, st);
+    case 4:
+      if (!fits(F ? 1024 : 512)) return 1;
+      return F ? launch_tiled<R, 4, 4>(p, psi, y, st) : launch_tiled<R, 4, 2>(p, psi, y, st);
+    case 8:
+      if (!fits(F ? 512 : 256)) return 1;
+      return F ? launch_tiled<R, 8, 2>(p, psi, y, st) : launch_tiled<R, 8, 1>(p, psi, y, st);
+    case 16:
+      if (!fits(F ? 512 : 256)) return 1;
+      return F ? launch_tiled<R, 16, 2>(p, psi, y, st) : launch_tiled<R, 16, 1>(p, psi, y, st);
+    default:
+      return 1;
+  }
 }
 
 // chi_i |x> = (1/sqrt 2) (-1)^{popcount(x & ((1<<k)-1))} f_i(x_k) |x ^ (1<<k)>,

@@ -5,6 +5,7 @@
 
 #include <cstdarg>
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -33,7 +34,7 @@ void clear_error();
 // Device copies of the grouped coefficient tables (see syk_terms.cpp for the math).
 struct DeviceTables {
   int device = -1;
-  uint4* m4_rec = nullptr;    // popcount-4 X-masks: {compact xor, zeta0, packed support, 0}
+  uint4* m4_rec = nullptr;    // popcount-4 X-masks: {compact xor, zeta0, packed support, row-flip patterns}
   double2* m4_t64 = nullptr;  // 32 entries per mask: T[u], then -T[u]
   float2* m4_t32 = nullptr;
   uint4* m2_rec = nullptr;    // popcount-2 X-masks: {compact xor, zeta_f, a | b<<8, 0}
@@ -41,6 +42,7 @@ struct DeviceTables {
   float2* m2_t32 = nullptr;
   double* wd64 = nullptr;     // n x n upper triangle: diagonal couplings w_cd
   float* wd32 = nullptr;
+  int* status = nullptr;      // device status word of the matvec (bounded-wait timeouts)
 };
 
 // Everything apply_H needs, by value, for one launch.
@@ -54,7 +56,13 @@ struct ApplyParams {
   const void* m4_tab;
   const void* m2_tab;
   const void* wd;
+  int* status;
+  const syk_terms* terms;  // host-side: tile-group lists
 };
+
+// Groups of X-masks sharing the compact-mask bits above a tile of 2^tb rows:
+// {h, first popcount-4 mask, end, first popcount-2 mask | end << 16}.
+int tile_groups(const syk_terms* t, int tb, const int4** dev, int* count);
 
 int ensure_device_tables(const syk_terms* t);
 int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p);
@@ -90,5 +98,6 @@ struct syk_terms {
   std::vector<double> m2_tab;    // n2 * n * 4 * 2
   std::vector<double> wdiag;     // n * n
   mutable syk::DeviceTables dev;
+  mutable std::map<int, std::pair<int4*, int>> groups_dev;  // tile bits -> device group list
   mutable std::mutex mtx;
 };

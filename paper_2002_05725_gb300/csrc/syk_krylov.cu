@@ -525,7 +525,8 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
         k_tridiag_eig<<<int(B), 32, smem, st>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem,
                                                 tol, ws.theta, ws.Q, ws.sb, ws.status);
         k_step_min<<<1, 32, 0, st>>>(int(B), ws.sb, ws.sacc);
-        SYK_CUDA_CHECK(cudaMemcpyAsync(hstat, ws.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+        SYK_CUDA_CHECK(cudaMemcpyAsync(hstat, ws.status, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        SYK_CUDA_CHECK(cudaMemcpyAsync(hstat + 2, P.status, sizeof(int), cudaMemcpyDeviceToHost, st));
         SYK_CUDA_CHECK(cudaMemcpyAsync(hs, ws.sacc, sizeof(double), cudaMemcpyDeviceToHost, st));
         SYK_CUDA_CHECK(cudaStreamSynchronize(st));
         prof_collect();
@@ -536,6 +537,10 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
         if (hstat[0] & 2) {
           set_error("expmv: tridiagonal eigensolver did not converge");
           return SYK_ENUMERIC;
+        }
+        if (hstat[2] & 4) {
+          set_error("apply_H: a bounded wait for a staged tile gave up");
+          return SYK_ETIMEOUT;
         }
         if (last || *hs >= s_rem) {
           m_eff = mm;

@@ -24,6 +24,7 @@
 //   W_c[u] = sum_{T with spin c} w'_T (-1)^popcount(s_T & u).
 // * m = 0 (two spins c<d, both Majoranas each): z_T = e_c ^ e_d and
 //   c_0(x) = sum_{c<d} w_cd (-1)^(x_c + x_d), w_cd real.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -142,6 +143,16 @@ extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
           }
     const uint64_t Dmask = uint64_t(t->D) - 1;
     t->wdiag.assign(size_t(n) * n, 0.0);
+    struct Rec4 {
+      uint32_t mc, zeta, supp, flips;
+      std::complex<double> tab[16];
+    };
+    struct Rec2 {
+      uint32_t mc, zeta, ab;
+      std::vector<std::complex<double>> W;
+    };
+    std::vector<Rec4> r4;
+    std::vector<Rec2> r2;
     for (auto& kv : groups) {
       const uint64_t m = kv.first;
       const auto& terms = kv.second;
@@ -157,7 +168,7 @@ extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
           t->wdiag[size_t(c) * n + d] += w.real();
         }
       } else if (pc == 4) {
-        std::complex<double> tab[16];
+        Rec4 r{};
         const uint64_t zeta0 = t->zm[terms[0]] & ~m;
         for (int64_t T : terms) {
           const uint64_t z = t->zm[T];
@@ -165,56 +176,79 @@ extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
           const uint32_t s = syk::extract_bits(z, m);
           std::complex<double> w = t->J[T] * syk::ipow(t->ph[T]) / 4.0;
           if (__builtin_popcountll(z & m) & 1) w = -w;
-          for (int u = 0; u < 16; ++u) tab[u] += (__builtin_popcount(s & u) & 1) ? -w : w;
+          for (int u = 0; u < 16; ++u) r.tab[u] += (__builtin_popcount(s & u) & 1) ? -w : w;
         }
-        uint32_t supp = 0;
-        int o = 0;
+        int pos[4], o = 0;
         for (int k = 0; k < n; ++k)
-          if ((m >> k) & 1) supp |= uint32_t(k) << (8 * (o++));
-        t->m4_rec.push_back(uint32_t(m & Dmask));
-        t->m4_rec.push_back(uint32_t(zeta0));
-        t->m4_rec.push_back(supp);
-        t->m4_rec.push_back(0u);
-        for (int u = 0; u < 32; ++u) {
-          std::complex<double> v = u < 16 ? tab[u] : -tab[u - 16];
-          t->m4_tab.push_back(v.real());
-          t->m4_tab.push_back(v.imag());
+          if ((m >> k) & 1) pos[o++] = k;
+        r.mc = uint32_t(m & Dmask);
+        r.zeta = uint32_t(zeta0);
+        r.supp = uint32_t(pos[0]) | uint32_t(pos[1]) << 8 | uint32_t(pos[2]) << 16 | uint32_t(pos[3]) << 24;
+        // Table-index change when compact row bit j flips (j = 8, 9, 10): bit j of the full
+        // index flips and so does the top bit n-1 (the parity of the compact index).
+        const int top = n - 1;
+        for (int b = 0; b < 3; ++b) {
+          const int j = 8 + b;
+          uint32_t f = 0;
+          if (j < top) {
+            for (int k = 0; k < 4; ++k)
+              if (pos[k] == j || pos[k] == top) f |= 1u << k;
+            if (((zeta0 >> j) & 1) ^ ((zeta0 >> top) & 1)) f |= 16u;
+          }
+          r.flips |= f << (5 * b);
         }
-        t->n4++;
+        r4.push_back(r);
       } else if (pc == 2) {
-        std::vector<std::complex<double>> W(size_t(n) * 4);
+        Rec2 r{};
+        r.W.assign(size_t(n) * 4, 0.0);
         uint64_t zetaf = 0;
         bool first = true;
         for (int64_t T : terms) {
           const int c = dbl[T];
           if (c < 0) throw std::runtime_error("popcount-2 term without a doubled spin");
           const uint64_t z = t->zm[T];
-          const uint64_t r = z ^ (uint64_t(1) << c);
+          const uint64_t rr = z ^ (uint64_t(1) << c);
           if (first) {
-            zetaf = r & ~m;
+            zetaf = rr & ~m;
             first = false;
-          } else if ((r & ~m) != zetaf) {
+          } else if ((rr & ~m) != zetaf) {
             throw std::runtime_error("popcount-2 group: zeta_f differs");
           }
-          const uint32_t s = syk::extract_bits(r, m);
+          const uint32_t s = syk::extract_bits(rr, m);
           std::complex<double> w = t->J[T] * syk::ipow(t->ph[T]) / 4.0;
           if (__builtin_popcountll(z & m) & 1) w = -w;
-          for (int u = 0; u < 4; ++u) W[size_t(c) * 4 + u] += (__builtin_popcount(s & u) & 1) ? -w : w;
+          for (int u = 0; u < 4; ++u) r.W[size_t(c) * 4 + u] += (__builtin_popcount(s & u) & 1) ? -w : w;
         }
         const int a = __builtin_ctzll(m), b = 63 - __builtin_clzll(m);
-        t->m2_rec.push_back(uint32_t(m & Dmask));
-        t->m2_rec.push_back(uint32_t(zetaf));
-        t->m2_rec.push_back(uint32_t(a) | (uint32_t(b) << 8));
-        t->m2_rec.push_back(0u);
-        for (auto& v : W) {
-          t->m2_tab.push_back(v.real());
-          t->m2_tab.push_back(v.imag());
-        }
-        t->n2++;
+        r.mc = uint32_t(m & Dmask);
+        r.zeta = uint32_t(zetaf);
+        r.ab = uint32_t(a) | (uint32_t(b) << 8);
+        r2.push_back(std::move(r));
       } else {
         throw std::runtime_error("X-mask with odd popcount or popcount > 4");
       }
     }
+    // Tables are sorted by the compact XOR mask, so masks sharing the bits above any
+    // tile size form contiguous ranges (the tiled matvec walks them group by group).
+    std::sort(r4.begin(), r4.end(), [](const Rec4& a, const Rec4& b) { return a.mc < b.mc; });
+    std::sort(r2.begin(), r2.end(), [](const Rec2& a, const Rec2& b) { return a.mc < b.mc; });
+    for (const Rec4& r : r4) {
+      t->m4_rec.insert(t->m4_rec.end(), {r.mc, r.zeta, r.supp, r.flips});
+      for (int u = 0; u < 32; ++u) {
+        const std::complex<double> v = u < 16 ? r.tab[u] : -r.tab[u - 16];
+        t->m4_tab.push_back(v.real());
+        t->m4_tab.push_back(v.imag());
+      }
+    }
+    for (const Rec2& r : r2) {
+      t->m2_rec.insert(t->m2_rec.end(), {r.mc, r.zeta, r.ab, 0u});
+      for (const auto& v : r.W) {
+        t->m2_tab.push_back(v.real());
+        t->m2_tab.push_back(v.imag());
+      }
+    }
+    t->n4 = int(r4.size());
+    t->n2 = int(r2.size());
     for (double v : t->J)
       if (!std::isfinite(v)) throw std::runtime_error("non-finite coupling");
   } catch (const std::bad_alloc&) {
@@ -236,10 +270,12 @@ extern "C" void syk_free_terms(syk_terms* t) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(t->dev.device);
-    void* ptrs[] = {t->dev.m4_rec, t->dev.m4_t64, t->dev.m4_t32, t->dev.m2_rec,
-                    t->dev.m2_t64, t->dev.m2_t32, t->dev.wd64,  t->dev.wd32};
+    void* ptrs[] = {t->dev.m4_rec, t->dev.m4_t64, t->dev.m4_t32, t->dev.m2_rec, t->dev.m2_t64,
+                    t->dev.m2_t32, t->dev.wd64,   t->dev.wd32,   t->dev.status};
     for (void* p : ptrs)
       if (p) cudaFree(p);
+    for (auto& kv : t->groups_dev)
+      if (kv.second.first) cudaFree(kv.second.first);
     if (prev >= 0) cudaSetDevice(prev);
   }
   delete t;
@@ -302,6 +338,8 @@ int ensure_device_tables(const syk_terms* t) {
   SYK_TRY(upload(&d.m2_t32, f2.data(), f2.size() * 4));
   SYK_TRY(upload(&d.wd64, t->wdiag.data(), t->wdiag.size() * 8));
   SYK_TRY(upload(&d.wd32, fd.data(), fd.size() * 4));
+  SYK_TRY(upload(&d.status, nullptr, 16));
+  SYK_CUDA_CHECK(cudaMemset(d.status, 0, 16));
   d.device = cur;
   return SYK_OK;
 }
@@ -331,6 +369,38 @@ int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p)
   p->m4_tab = f ? (const void*)t->dev.m4_t32 : (const void*)t->dev.m4_t64;
   p->m2_tab = f ? (const void*)t->dev.m2_t32 : (const void*)t->dev.m2_t64;
   p->wd = f ? (const void*)t->dev.wd32 : (const void*)t->dev.wd64;
+  p->status = t->dev.status;
+  p->terms = t;
+  return SYK_OK;
+}
+
+int tile_groups(const syk_terms* t, int tb, const int4** out, int* count) {
+  SYK_TRY(ensure_device_tables(t));
+  std::lock_guard<std::mutex> lock(t->mtx);
+  auto it = t->groups_dev.find(tb);
+  if (it == t->groups_dev.end()) {
+    std::vector<int4> g;
+    size_t i4 = 0, i2 = 0;
+    const size_t n4 = size_t(t->n4), n2 = size_t(t->n2);
+    bool diag = false;
+    while (i4 < n4 || i2 < n2 || !diag) {
+      uint32_t h = 0xffffffffu;
+      if (i4 < n4) h = std::min(h, t->m4_rec[4 * i4] >> tb);
+      if (i2 < n2) h = std::min(h, t->m2_rec[4 * i2] >> tb);
+      if (!diag) h = 0;
+      const size_t b4 = i4, b2 = i2;
+      while (i4 < n4 && (t->m4_rec[4 * i4] >> tb) == h) ++i4;
+      while (i2 < n2 && (t->m2_rec[4 * i2] >> tb) == h) ++i2;
+      if (h == 0) diag = true;
+      g.push_back(make_int4(int(h), int(b4), int(i4), int(b2 | (i2 << 16))));
+    }
+    int4* d = nullptr;
+    SYK_CUDA_CHECK(cudaMalloc(&d, g.size() * sizeof(int4)));
+    SYK_CUDA_CHECK(cudaMemcpy(d, g.data(), g.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    it = t->groups_dev.emplace(tb, std::make_pair(d, int(g.size()))).first;
+  }
+  *out = it->second.first;
+  *count = it->second.second;
   return SYK_OK;
 }
 
