@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark: regularized-OTOC curves per hour at N = 40 on GB300.
+
+One step = the regularized OTOC F~(t) (Eq. F_reg, rho^{1/4} between the
+operators, W = chi_0, V = chi_1, beta J = 10) of B random states of one
+coupling draw on a 10-point time grid t = 1.2, 2.4, ..., 12 plus t = 0 (the
+10-point curves of Supp. Table I, to the t = 12 of the batched workload),
+Krylov dimension 40, tolerance 1e-7, complex64 vectors with FP64 Lanczos
+scalars.  value = curves (states) per hour over all ranks; each rank runs its
+own coupling draw (independent replicas, weak scaling, no collective on the
+data path).  Inputs are synthetic (Gaussian couplings and states, seeded).
+
+--impl reference times the CPU oracle (plain-C term-at-a-time H|psi>) on a
+bounded sample of rows and converts it to the same metric with a modelled
+count of H applications per curve (see applies_model).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--N", type=int, default=40)
+    ap.add_argument("--states", type=int, default=8)
+    ap.add_argument("--beta", type=float, default=10.0)
+    ap.add_argument("--npts", type=int, default=10)
+    ap.add_argument("--tmax", type=float, default=12.0)
+    ap.add_argument("--krylov", type=int, default=40)
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def time_grid(npts, tmax):
+    return [0.0] + [round(tmax * k / npts, 12) for k in range(1, npts + 1)]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x clock."""
+    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ cost model
+def applies_model(N, beta, times, m=40, tol=1e-7):
+    """Modelled H applications per state for one OTOC curve (Lanczos, checks every 8).
+
+    A Krylov step of length tau needs the smallest m with (e rho tau / 2m)^m <= tol,
+    rho = half the spectral width (~0.043 N J for SYK); longer steps are split.
+    """
+    rho = 0.043 * N
+
+    def m_needed(tau):
+        if tau <= 0:
+            return 0
+        for mm in range(1, 400):
+            if (math.e * rho * tau / (2 * mm)) ** mm <= tol:
+                return mm
+        return 400
+
+    def applies(tau):
+        if tau <= 0:
+            return 0
+        k = 1
+        while m_needed(tau / k) > m:
+            k += 1
+        return k * min(m, 8 * math.ceil(m_needed(tau / k) / 8))
+
+    total = applies(beta / 8) + applies(beta / 4)
+    prev = 0.0
+    for t in times:
+        total += 2 * applies(t - prev) + 2 * applies(t) + 2 * applies(beta / 4)
+        prev = t
+    return total
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                if int(f[0]) != self.index:
+                    continue
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_apply_seconds(N, states, budget_s, seed=0):
+    """Times the oracle's plain-C H|psi> on sampled rows; returns (s per full apply, info)."""
+    from oracle import capply
+    from paper_2002_05725_gb300 import inputs
+    cores = os.cpu_count() or 1
+    J = inputs.couplings(N, seed)
+    tl = capply.TermList(N, J)
+    D = inputs.sector_dim(N)
+    rng = np.random.default_rng(1)
+    psi = (rng.standard_normal((D, states)) + 1j * rng.standard_normal((D, states))).astype(np.complex128)
+    rows = rng.integers(0, D, 4 * cores)
+    t0 = time.perf_counter()
+    capply.apply_H(tl, 0, psi, rows=rows, nthreads=cores)
+    dt = time.perf_counter() - t0
+    nrows = int(min(D, max(len(rows), len(rows) * budget_s / max(dt, 1e-6))))
+    rows = rng.integers(0, D, nrows)
+    t0 = time.perf_counter()
+    capply.apply_H(tl, 0, psi, rows=rows, nthreads=cores)
+    dt = time.perf_counter() - t0
+    per_apply = dt * D / nrows
+    return per_apply, {"rows": nrows, "seconds": dt, "cores": cores, "terms": len(tl.m)}
+
+
+def reference_main(a, rank, world):
+    times = time_grid(a.npts, a.tmax)
+    A = applies_model(a.N, a.beta, times[1:], a.krylov, a.tol)
+    if rank != 0:
+        return
+    budget = max(2.0, min(30.0, 120.0 / max(1, a.steps + a.warmup)))
+    vals = []
+    info = None
+    for s in range(a.warmup + a.steps):
+        per_apply, info = oracle_apply_seconds(a.N, a.states, budget, seed=s)
+        if s >= a.warmup:
+            vals.append(per_apply)
+    per_apply = statistics.median(vals)
+    curve_s = per_apply * A  # all states of the batch advance together in one apply
+    value = a.states * 3600.0 / curve_s
+    line = {
+        "impl": "reference", "metric": "OTOC curves/hour at N=40", "value": value, "unit": "curves/hour",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_apply * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(a, times),
+        "cpu_baseline": {"value": value, "unit": "curves/hour", "cores": info["cores"], "kind": "oracle",
+                         "sample": f"plain-C fp64 term-at-a-time H|psi> on {info['rows']} sampled rows x "
+                                   f"{a.states} states per step (of {inputs_dim(a.N)}), scaled to full applies x "
+                                   f"{A} modelled H applications per curve"},
+        "e2e": {"value": value, "unit": "curves/hour", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def inputs_dim(N):
+    return 1 << (N // 2 - 1)
+
+
+def config_dict(a, times):
+    return {"workload": f"regularized OTOC F~(t), N={a.N} (sector dim 2^{a.N // 2 - 1}), beta*J={a.beta:g}, "
+                        f"W=chi_0 V=chi_1, {a.states} Gaussian random states per coupling draw, "
+                        f"t=0 and {a.npts} points to t={a.tmax:g}, Krylov dim {a.krylov}, tol {a.tol:g}",
+            "N": a.N, "beta_J": a.beta, "states_per_step": a.states, "t_grid": times, "krylov_dim": a.krylov,
+            "tol": a.tol, "vector_dtype": a.dtype, "scalars": "f64",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_main(a, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_05725_gb300 import inputs, syk
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    syk.load()
+    times = time_grid(a.npts, a.tmax)
+    realization = rank
+    J = inputs.couplings(a.N, seed=0, realization=realization)
+    terms = syk.syk_build_terms(a.N, J)
+    host = inputs.random_states(a.N, a.states, seed=0, realization=realization)
+    cdt = torch.complex64 if a.dtype == "c64" else torch.complex128
+    psi_host = torch.from_numpy(np.ascontiguousarray(host.T)).to(cdt).pin_memory()
+    psi_dev = psi_host.to(dev).contiguous()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(src):
+        return syk.syk_otoc(terms, a.beta, 0, 1, times, src, krylov_dim=a.krylov, tol=a.tol)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(a.warmup):
+        F = step(psi_dev)
+    barrier()
+
+    # timed region: device-resident inputs
+    syk.syk_counters(reset=True)
+    syk.syk_profile_read(reset=True)
+    syk.syk_profile_enable(True)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    total_ms = 0.0
+    for _ in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        F = step(psi_dev)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += e0.elapsed_time(e1)
+    clocks = clk.stop()
+    syk.syk_profile_enable(False)
+    prof = syk.syk_profile_read(reset=True)
+    cnt = syk.syk_counters(reset=True)
+    barrier()
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * a.states * a.steps * 3600.0 / (t_max / 1e3)
+
+    # end to end: host (pinned) inputs through the C ABI, result read back to host
+    e2e_ms = 0.0
+    for _ in range(a.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        F = step(psi_host.numpy())
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_max = e2e_ms
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_max = float(t.item())
+    e2e_val = world * a.states * a.e2e_steps * 3600.0 / (e2e_max / 1e3) if a.e2e_steps else None
+
+    if rank != 0:
+        return
+    Ft = F / F[0]
+    applies_per_state = cnt["h_applies"] / max(1, a.steps) / a.states
+    D = terms.D
+    nnz = D * terms.nmasks
+    avg_ms = prof["total_ms"] / max(1, prof["launches"])
+    flops = 8.0 * nnz * a.states
+    pk, pk_kind = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    bound, unit, peak = "alu", "TFLOP/s", fp32_peak_tflops(sm_mhz)
+    if a.dtype == "c128":
+        peak = peak / 64.0  # FP64 FMA rate of GB300 is 1/64 of FP32
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    esz = 8 if a.dtype == "c64" else 16
+    gather = nnz * a.states * esz / (avg_ms * 1e-3) / 1e9
+    line = {
+        "metric": "OTOC curves/hour at N=40", "value": value, "unit": "curves/hour", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
+        "config": config_dict(a, times),
+        "roofline": {"kernel": "apply_H (k_apply_tiled)", "bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
+                                  + (" / 64 (FP64)" if a.dtype == "c128" else ""),
+                     "per_launch": {"flops": flops, "avg_ms": avg_ms, "launches": prof["launches"]}},
+        "hpsi": {"gather_GBps": gather, "hbm_peak_GBps": pk.get("hbm_gbs"), "gather_frac_of_hbm":
+                 gather / float(pk.get("hbm_gbs", 6800.0)), "peak_kind": pk_kind},
+        "applies_per_curve": applies_per_state,
+        "applies_per_curve_model": applies_model(a.N, a.beta, times[1:], a.krylov, a.tol),
+        "krylov_bases_per_step": cnt["krylov_bases"] / max(1, a.steps),
+        "gpu_launches": cnt["launches"],
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": "curves/hour", "h2d_bytes_per_step": int(D * a.states * esz),
+                "d2h_bytes_per_step": int(len(times) * a.states * 16)},
+        "result_check": {"Ftilde_t0": float(np.real(Ft[0, 0])), "Ftilde_tmax_mean": float(np.mean(np.real(Ft[-1])))},
+    }
+    if not a.no_cpu_baseline and world == 1:
+        per_apply, info = oracle_apply_seconds(a.N, a.states, a.cpu_seconds)
+        curve_s = per_apply * applies_per_state
+        line["cpu_baseline"] = {
+            "value": a.states * 3600.0 / curve_s, "unit": "curves/hour", "cores": info["cores"], "kind": "oracle",
+            "sample": f"plain-C fp64 term-at-a-time H|psi> (oracle/c/apply_terms.c) on {info['rows']} sampled rows "
+                      f"x {a.states} states ({info['seconds']:.1f} s), scaled to full applies x "
+                      f"{applies_per_state:.0f} H applications per curve counted on the GPU path"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        reference_main(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        gpu_main(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -148,9 +148,9 @@ int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t,
 const char* syk_last_error(void);
 
 /* syk_counters -- counters since the last reset (any pointer may be NULL):
- * H applications per state (batch counted once per state), Krylov bases.
- * reset != 0 zeroes them after reading. */
-int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int reset);
+ * H applications per state (a batch of B states counts B), Krylov bases, and
+ * kernel launches made by the library.  reset != 0 zeroes them after reading. */
+int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int64_t* launches, int reset);
 
 /* syk_profile_enable / syk_profile_read -- CUDA-event timing of every apply_H
  * launch the library makes (on the stream it is launched on).  While enabled,

@@ -117,6 +117,7 @@ void launch_one(const ApplyParams& p, const void* psi, void* y, int64_t ld, int6
   int64_t blocks = (p.D + threads - 1) / threads;
   blocks = std::min<int64_t>(blocks, 152 * 64);
   k_apply_rows<R, BT><<<(unsigned)blocks, threads, 0, st>>>(p, static_cast<const C*>(psi), static_cast<C*>(y), ld, b0);
+  count_launch();
 }
 
 template <typename R>
@@ -398,6 +399,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   const unsigned blocks = (unsigned)(p.D / Cfg::T);
   k_apply_tiled<R, BT, RPT><<<blocks, Cfg::NT, Cfg::SMEM, st>>>(p, groups, ng, static_cast<const C*>(psi),
                                                                  static_cast<C*>(y));
+  count_launch();
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
 }
@@ -482,6 +484,7 @@ int launch_apply_chi(int N, int i, int parity_in, int dtype, const void* psi, vo
   else
     k_apply_chi<double><<<(unsigned)blocks, threads, 0, st>>>(n, i, 1 - parity_in, D, batch,
                                                               static_cast<const double2*>(psi), static_cast<double2*>(y));
+  count_launch();
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
 }

@@ -79,6 +79,7 @@ void prof_after_apply(cudaStream_t st);
 void prof_collect();
 void count_applies(int64_t states);
 void count_bases(int64_t n);
+void count_launch(int64_t n = 1);
 
 inline size_t dtype_size(int dtype) { return dtype == SYK_C64 ? 8 : 16; }
 inline bool dtype_ok(int dtype) { return dtype == SYK_C64 || dtype == SYK_C128; }

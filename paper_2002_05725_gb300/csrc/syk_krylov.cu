@@ -377,24 +377,29 @@ struct Ops {
     dim3 grid(ws.G, nk);
     k_dots<R><<<grid, ws.bdim, ws.bdim * sizeof(double2), st>>>(k0, (const C*)V, vs, (const C*)w, ws.D * ws.B,
                                                                  (int)ws.B, ws.part);
+    count_launch();
   }
   static void update(const KrylovWS& ws, int nk, const void* V, size_t vs, const double2* h, void* w, double* np,
                      cudaStream_t st) {
     k_update<R><<<ws.G, ws.bdim, ws.bdim * sizeof(double2), st>>>(nk, (const C*)V, vs, h, (C*)w, ws.D * ws.B,
                                                                    (int)ws.B, np);
+    count_launch();
   }
   static void scale(const KrylovWS& ws, const void* src, void* dst, const double* inv, cudaStream_t st) {
     k_scale<R><<<ws.G, ws.bdim, 0, st>>>((const C*)src, (C*)dst, inv, ws.D * ws.B, (int)ws.B);
+    count_launch();
   }
   static void combine(const KrylovWS& ws, int nk, const double2* c, void* out, cudaStream_t st) {
     k_combine<R><<<ws.G, ws.bdim, 0, st>>>(nk, (const C*)ws.V, (size_t)(ws.D * ws.B), c, (C*)out, ws.D * ws.B,
                                            (int)ws.B);
+    count_launch();
   }
 };
 
 void reduce_parts(const KrylovWS& ws, int nk, double2* out, cudaStream_t st) {
   const int n = nk * (int)ws.B;
   k_reduce_parts<<<(n + 127) / 128, 128, 0, st>>>(nk, ws.G, (int)ws.B, ws.part, out);
+  count_launch();
 }
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
@@ -503,6 +508,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
     Ops<R>::dots(ws, 0, 1, cur, 0, cur, st);
     reduce_parts(ws, 1, ws.h1, st);
     k_norm_init<<<(int(B) + 127) / 128, 128, 0, st>>>(int(B), ws.h1, ws.beta0, ws.inv, ws.status);
+    count_launch();
     Ops<R>::scale(ws, cur, ws.vec(0), ws.inv, st);
     int m_eff = m;
     for (int j = 0; j < m; ++j) {
@@ -517,6 +523,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
       Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
       k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, ws.h2, ws.npart, ws.alpha,
                                                                ws.beta, ws.inv, ws.status, bt);
+      count_launch();
       if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
       const bool last = (j + 1 == m);
       if (last || ((j + 1) % 8 == 0)) {
@@ -525,6 +532,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
         k_tridiag_eig<<<int(B), 32, smem, st>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem,
                                                 tol, ws.theta, ws.Q, ws.sb, ws.status);
         k_step_min<<<1, 32, 0, st>>>(int(B), ws.sb, ws.sacc);
+        count_launch(2);
         SYK_CUDA_CHECK(cudaMemcpyAsync(hstat, ws.status, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
         SYK_CUDA_CHECK(cudaMemcpyAsync(hstat + 2, P.status, sizeof(int), cudaMemcpyDeviceToHost, st));
         SYK_CUDA_CHECK(cudaMemcpyAsync(hs, ws.sacc, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -554,6 +562,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
       return SYK_ENUMERIC;
     }
     k_tridiag_coef<<<int(B), 64, 0, st>>>(m_eff, int(B), ws.theta, ws.Q, ws.beta0, zr, zi, nullptr, s_acc, ws.c);
+    count_launch();
     Ops<R>::combine(ws, m_eff, ws.c, out, st);
     SYK_CUDA_CHECK(cudaGetLastError());
     count_bases(1);
@@ -660,6 +669,7 @@ extern "C" int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const
   const size_t smem = sizeof(double) * (size_t(m) * m + 2 * m + 2);
   k_tridiag_eig<<<B, 32, smem, st>>>(m, B, alpha, bpad, nullptr, z_re, z_im, 1.0, 1.0, theta, Q, sb, status);
   k_tridiag_coef<<<B, 64, 0, st>>>(m, B, theta, Q, beta0, z_re, z_im, nullptr, 1.0, (double2*)out);
+  count_launch(2);
   cudaError_t e = cudaGetLastError();
   int hstat = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st);

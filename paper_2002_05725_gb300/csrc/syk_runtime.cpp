@@ -12,6 +12,7 @@ namespace {
 
 std::atomic<int64_t> g_applies{0};
 std::atomic<int64_t> g_bases{0};
+std::atomic<int64_t> g_launches{0};
 
 struct Prof {
   std::mutex mtx;
@@ -41,6 +42,7 @@ thread_local cudaEvent_t t_start = nullptr;
 
 void count_applies(int64_t states) { g_applies += states; }
 void count_bases(int64_t n) { g_bases += n; }
+void count_launch(int64_t n) { g_launches += n; }
 
 void prof_before_apply(cudaStream_t st) {
   Prof& p = prof();
@@ -97,12 +99,14 @@ void* pinned_scratch(size_t bytes) {
 
 }  // namespace syk
 
-extern "C" int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int reset) {
+extern "C" int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int64_t* launches, int reset) {
   if (h_applies) *h_applies = syk::g_applies.load();
   if (krylov_bases) *krylov_bases = syk::g_bases.load();
+  if (launches) *launches = syk::g_launches.load();
   if (reset) {
     syk::g_applies = 0;
     syk::g_bases = 0;
+    syk::g_launches = 0;
   }
   return SYK_OK;
 }

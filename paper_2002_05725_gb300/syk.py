@@ -56,7 +56,7 @@ def load(build_if_missing: bool = False):
         "syk_correlator_G": (i32, [vp, dbl, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp, vp]),
         "syk_otoc": (i32, [vp, dbl, i32, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp]),
         "syk_last_error": (ctypes.c_char_p, []),
-        "syk_counters": (i32, [vp, vp, i32]),
+        "syk_counters": (i32, [vp, vp, vp, i32]),
         "syk_profile_enable": (i32, [i32]),
         "syk_profile_read": (i32, [vp, vp, i32]),
     }
@@ -235,9 +235,9 @@ def syk_otoc(terms: Terms, beta: float, i: int, j: int, times, psi0, krylov_dim:
 
 
 def syk_counters(reset: bool = False):
-    a, b = ctypes.c_int64(), ctypes.c_int64()
-    _check(load().syk_counters(ctypes.byref(a), ctypes.byref(b), int(reset)), "syk_counters")
-    return {"h_applies": a.value, "krylov_bases": b.value}
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().syk_counters(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(reset)), "syk_counters")
+    return {"h_applies": a.value, "krylov_bases": b.value, "launches": c.value}
 
 
 def syk_profile_enable(on: bool = True):
