@@ -117,6 +117,30 @@ int syk_expmv(const syk_terms* terms, int parity, int dtype, double z_re, double
               const void* psi, void* out, int64_t batch, int krylov_dim, double tol,
               void* workspace, size_t ws_bytes, void* stream, int* nsteps);
 
+/* syk_expmv_static -- syk_expmv with its workspace in a fixed array of device
+ * memory inside the library, so the call itself allocates nothing.  The paper
+ * has no counterpart; this entry point is for callers that cannot allocate
+ * device memory when they call: services whose device memory is budgeted up
+ * front and must not fail with out-of-memory mid-run, hosts that route every
+ * device allocation through their own pool, and latency-critical loops where
+ * cudaMalloc/cudaFree would stall or synchronise the device.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ * Limit: the scratch array is SYK_STATIC_SCRATCH_BYTES (16 MiB) of static
+ * device memory, held by every GPU that loads the library until the process
+ * exits; a call whose syk_workspace_bytes(N, dtype, krylov_dim, batch, 0)
+ * exceeds it fails with SYK_ENOMEM.  The term set must already be on the
+ * current device (any earlier call with it on this device uploads it), else
+ * SYK_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call uses the same array, which keeps the previous call's
+ * contents (the call zeroes what must start at zero); calls that overlap on the
+ * GPU (other streams or host threads) race on it, so the caller must
+ * serialise them.  Arguments, results and other errors as syk_expmv. */
+#define SYK_STATIC_SCRATCH_BYTES (16u << 20)
+int syk_expmv_static(const syk_terms* terms, int parity, int dtype, double z_re, double z_im,
+                     const void* psi, void* out, int64_t batch, int krylov_dim, double tol,
+                     void* stream, int* nsteps);
+
 /* ------------------------------------------------------------- correlators
  * syk_correlator_G -- real-time two-point function, Eq. G with Eq.
  * q_typicality: for each of `nstates` states psi~ (in the EVEN sector),

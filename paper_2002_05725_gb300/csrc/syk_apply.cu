@@ -389,7 +389,11 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   while ((1 << tb) < Cfg::T) ++tb;
   const int4* groups = nullptr;
   int ng = 0;
-  SYK_TRY(tile_groups(p.terms, tb, &groups, &ng));
+  if (p.no_alloc) {
+    if (!tile_groups_cached(p.terms, tb, &groups, &ng)) return 1;  // row kernel instead
+  } else {
+    SYK_TRY(tile_groups(p.terms, tb, &groups, &ng));
+  }
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "syk_cplx.cuh"
 #include "syk_krylov.cuh"
@@ -493,7 +494,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
   const int m = ws.m;
   const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
   const double zr = z.real(), zi = z.imag();
-  int* hstat = static_cast<int*>(pinned_scratch(64));
+  int* hstat = static_cast<int*>(ws.host_stage ? ws.host_stage : pinned_scratch(64));
   double* hs = reinterpret_cast<double*>(hstat + 4);
   SYK_CUDA_CHECK(cudaMemsetAsync(ws.status, 0, sizeof(int) * 4, st));
   double s_rem = 1.0;
@@ -684,4 +685,70 @@ extern "C" int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const
     return SYK_ENUMERIC;
   }
   return SYK_OK;
+}
+
+// ---------------------------------------------------------------- static-scratch variant
+// Workspace of syk_expmv_static: one fixed array of device memory per GPU that
+// loads the library.  Host code only ever uses its device address, looked up
+// once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_expmv_static_scratch[SYK_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mtx;
+void* g_static_addr[128] = {};
+}  // namespace
+
+extern "C" int syk_expmv_static(const syk_terms* terms, int parity, int dtype, double z_re, double z_im,
+                                const void* psi, void* out, int64_t batch, int krylov_dim, double tol, void* stream,
+                                int* nsteps) {
+  clear_error();
+  if (!terms || !psi || !out || batch < 1 || batch > 256 || krylov_dim < 2 || krylov_dim > SYK_MAX_KRYLOV ||
+      !dtype_ok(dtype) || (parity != 0 && parity != 1)) {
+    set_error("syk_expmv_static: invalid argument (batch=%lld krylov_dim=%d dtype=%d parity=%d)", (long long)batch,
+              krylov_dim, dtype, parity);
+    return SYK_EINVAL;
+  }
+  if (!std::isfinite(z_re) || !std::isfinite(z_im)) {
+    set_error("syk_expmv_static: non-finite z");
+    return SYK_EINVAL;
+  }
+  int dev = -1;
+  SYK_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) {
+    set_error("syk_expmv_static: device ordinal %d out of range", dev);
+    return SYK_EINVAL;
+  }
+  const size_t need = krylov_ws_bytes(terms->D, dtype, krylov_dim, batch);
+  if (need > SYK_STATIC_SCRATCH_BYTES) {
+    set_error("syk_expmv_static: needs %zu bytes of workspace, more than the %u-byte static scratch; "
+              "use syk_expmv or a smaller batch or krylov_dim", need, (unsigned)SYK_STATIC_SCRATCH_BYTES);
+    return SYK_ENOMEM;
+  }
+  if (terms->dev.device != dev) {
+    set_error("syk_expmv_static: the term set is not on device %d yet; make any other call with it on this "
+              "device first (that call uploads it)", dev);
+    return SYK_EINVAL;
+  }
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mtx);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_expmv_static_scratch);
+      if (e != cudaSuccess || !p) {
+        set_error("syk_expmv_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return SYK_ECUDA;
+      }
+      g_static_addr[dev] = p;
+    }
+    base = g_static_addr[dev];
+  }
+  ApplyParams P;
+  SYK_TRY(make_apply_params(terms, parity, dtype, &P));
+  P.no_alloc = true;
+  KrylovWS ws;
+  SYK_TRY(krylov_ws_carve(&ws, base, SYK_STATIC_SCRATCH_BYTES, P.D, dtype, krylov_dim, batch));
+  alignas(16) unsigned char stage[64];
+  ws.host_stage = stage;
+  return expmv_impl(P, dtype, {z_re, z_im}, psi, out, batch, tol, ws, static_cast<cudaStream_t>(stream), nsteps);
 }

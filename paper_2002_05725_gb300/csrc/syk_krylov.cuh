@@ -29,6 +29,7 @@ struct KrylovWS {
   double* sacc = nullptr;    // 1
   double2* c = nullptr;      // m * B
   int* status = nullptr;     // 4 ints
+  void* host_stage = nullptr;  // host buffer (>= 64 B) for status reads; NULL: pinned scratch
   size_t vec_bytes() const { return size_t(D) * B * dtype_size(dtype); }
   char* vec(int k) const { return V + size_t(k) * vec_bytes(); }
 };

@@ -371,7 +371,17 @@ int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p)
   p->wd = f ? (const void*)t->dev.wd32 : (const void*)t->dev.wd64;
   p->status = t->dev.status;
   p->terms = t;
+  p->no_alloc = false;
   return SYK_OK;
+}
+
+bool tile_groups_cached(const syk_terms* t, int tb, const int4** out, int* count) {
+  std::lock_guard<std::mutex> lock(t->mtx);
+  auto it = t->groups_dev.find(tb);
+  if (it == t->groups_dev.end()) return false;
+  *out = it->second.first;
+  *count = it->second.second;
+  return true;
 }
 
 int tile_groups(const syk_terms* t, int tb, const int4** out, int* count) {

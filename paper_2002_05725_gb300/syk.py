@@ -53,6 +53,7 @@ def load(build_if_missing: bool = False):
         "syk_tridiag_expm": (i32, [i32, i64, vp, vp, vp, dbl, dbl, vp, vp]),
         "syk_workspace_bytes": (sz, [i32, i32, i32, i64, i32]),
         "syk_expmv": (i32, [vp, i32, i32, dbl, dbl, vp, vp, i64, i32, dbl, vp, sz, vp, vp]),
+        "syk_expmv_static": (i32, [vp, i32, i32, dbl, dbl, vp, vp, i64, i32, dbl, vp, vp]),
         "syk_correlator_G": (i32, [vp, dbl, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp, vp]),
         "syk_otoc": (i32, [vp, dbl, i32, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp]),
         "syk_last_error": (ctypes.c_char_p, []),
@@ -71,7 +72,7 @@ def load(build_if_missing: bool = False):
 def exported_symbols():
     """Names declared in include/syk.h that the loaded library must export."""
     return ["syk_build_terms", "syk_free_terms", "syk_terms_info", "syk_term_table", "syk_apply_H",
-            "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_correlator_G",
+            "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_expmv_static", "syk_correlator_G",
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read"]
 
 
@@ -190,6 +191,24 @@ def syk_expmv(terms: Terms, parity: int, z: complex, psi, krylov_dim: int = 40, 
     _check(load().syk_expmv(terms.ptr, int(parity), _dtype_code(p), z.real, z.imag, p.data_ptr(), y.data_ptr(),
                             p.shape[1], int(krylov_dim), float(tol), wptr, wbytes, _stream(stream),
                             ctypes.byref(ns)), "syk_expmv")
+    return y.reshape(psi.shape), ns.value
+
+
+def syk_expmv_static(terms: Terms, parity: int, z: complex, psi, krylov_dim: int = 40, tol: float = 1e-12,
+                     out=None, stream=None):
+    """syk_expmv with the library's fixed device scratch (no allocation by the call).
+
+    The term set must already be on the device (any earlier call uploads it).
+    Returns (e^{zH} psi, number of Krylov bases).
+    """
+    import torch
+    p = _as_cols(psi)
+    y = torch.empty_like(p) if out is None else _as_cols(out)
+    ns = ctypes.c_int(0)
+    z = complex(z)
+    _check(load().syk_expmv_static(terms.ptr, int(parity), _dtype_code(p), z.real, z.imag, p.data_ptr(),
+                                   y.data_ptr(), p.shape[1], int(krylov_dim), float(tol), _stream(stream),
+                                   ctypes.byref(ns)), "syk_expmv_static")
     return y.reshape(psi.shape), ns.value
 
 
