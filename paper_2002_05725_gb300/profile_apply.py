@@ -1,0 +1,47 @@
+"""Times syk_apply_H on one configuration (for profilers and quick measurements).
+
+    python -m paper_2002_05725_gb300.profile_apply --N 40 --batch 8 --dtype c64 --reps 3
+
+Prints one JSON line with the mean time per apply (CUDA events, after one
+warm-up apply) and the FP32/FP64 and effective-gather rates.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import inputs, syk
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--sector", type=int, default=0)
+    a = ap.parse_args()
+    import torch
+    syk.load()
+    dt = torch.complex64 if a.dtype == "c64" else torch.complex128
+    terms = syk.syk_build_terms(a.N, inputs.couplings(a.N, 0))
+    psi = inputs.random_states_device(a.N, a.batch, 1, "cuda", dt)
+    y = torch.empty_like(psi)
+    syk.syk_apply_H(terms, a.sector, psi, out=y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        syk.syk_apply_H(terms, a.sector, psi, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    nnz = terms.D * terms.nmasks
+    s = 8 if a.dtype == "c64" else 16
+    print(json.dumps({"N": a.N, "batch": a.batch, "dtype": a.dtype, "ms_per_apply": ms,
+                      "tflops": 8.0 * nnz * a.batch / (ms * 1e-3) / 1e12,
+                      "gather_GBps": nnz * a.batch * s / (ms * 1e-3) / 1e9, "nnz": nnz}))
+
+
+if __name__ == "__main__":
+    main()
