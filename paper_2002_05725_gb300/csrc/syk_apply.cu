@@ -16,10 +16,11 @@
 // psi[tile ^ h]; that tile (T * BT contiguous elements) is staged in shared
 // memory by a bulk asynchronous copy (cp.async.bulk + mbarrier), double
 // buffered so the next group's tile streams in during the current group's
-// arithmetic.  A thread owns RPT rows that differ in compact bits 8, 9, 10; the
-// table index of a popcount-4 mask for those rows follows from the first row's
-// by XOR with per-mask flip patterns, so the bit extraction is done once per
-// mask.  Rows wider than 16 bytes are read in 16-byte chunks in a lane-rotated
+// arithmetic.  A thread owns RPT rows that differ in the compact bits just above
+// the thread index (bits 6..10 depending on the CTA width); the table index of a
+// popcount-4 mask for those rows follows from the first row's by XOR with
+// per-mask flip patterns, so the bit extraction is done once per mask.  Small
+// sectors use narrower CTAs (64 or 128 threads) so that the grid fills the SMs.  Rows wider than 16 bytes are read in 16-byte chunks in a lane-rotated
 // order so that the 32 lanes of a warp hit distinct shared-memory banks.
 // k_apply_rows (fallback: any batch, any alignment, small sectors): one thread
 // per row, gathers straight from global memory.
@@ -35,6 +36,14 @@
 
 namespace syk {
 namespace {
+
+// Table index bits of a popcount-4 mask: bit k = bit pos_k of the full index xf.
+// s packs the right-shift pos_k - k of support bit k into byte k (funnel shifts use
+// only the low 5 bits of the amount).
+__device__ __forceinline__ uint32_t supp_bits(uint32_t xf, uint32_t s) {
+  return (__funnelshift_r(xf, 0u, s) & 1u) | (__funnelshift_r(xf, 0u, s >> 8) & 2u) |
+         (__funnelshift_r(xf, 0u, s >> 16) & 4u) | (__funnelshift_r(xf, 0u, s >> 24) & 8u);
+}
 
 template <typename R, int BT>
 __global__ void __launch_bounds__(128) k_apply_rows(ApplyParams p, const typename CT<R>::T* __restrict__ psi,
@@ -95,10 +104,7 @@ __global__ void __launch_bounds__(128) k_apply_rows(ApplyParams p, const typenam
     // popcount-4 masks: c_m(x) = T[(sign << 4) | u(x)]
     for (int k = 0; k < p.n4; ++k) {
       const uint4 rec = __ldg(&p.m4_rec[k]);
-      const uint32_t s = rec.z;
-      const uint32_t u = ((xf >> (s & 0xffu)) & 1u) | (((xf >> ((s >> 8) & 0xffu)) & 1u) << 1) |
-                         (((xf >> ((s >> 16) & 0xffu)) & 1u) << 2) | (((xf >> (s >> 24)) & 1u) << 3);
-      const uint32_t idx = u | ((__popc(rec.y & xf) & 1u) << 4);
+      const uint32_t idx = supp_bits(xf, rec.z) | ((__popc(rec.y & xf) & 1u) << 4);
       const C cf = __ldg(&t4[(size_t)k * 32 + idx]);
       const C* src = psi + (int64_t)(xc ^ rec.x) * ld + b0;
 #pragma unroll
@@ -234,26 +240,29 @@ __device__ __forceinline__ void pc2_coef(const C* __restrict__ t2, int k, int n,
   }
 }
 
-template <typename R, int BT, int RPT>
+template <typename R, int BT>
 struct TileCfg {
   using C = typename CT<R>::T;
-  static constexpr int NT = 256;
-  static constexpr int T = NT * RPT;  // rows per tile
+  // rows per thread: more rows share one table-index computation, fewer leave room
+  // for more resident warps
+  static constexpr int RPT = sizeof(R) == 4 ? (BT == 1 ? 8 : BT <= 4 ? 4 : BT == 8 ? 2 : 1)
+                                            : (BT == 1 ? 4 : BT <= 4 ? 2 : 1);
   static constexpr int ROWB = BT * (int)sizeof(C);
-  static constexpr int TILEB = T * ROWB;
   static constexpr int CH = ROWB >= 16 ? ROWB / 16 : 0;  // 16-byte chunks per row
   static constexpr int NS = CH ? CH : 1;
-  static constexpr size_t SMEM = 2 * (size_t)TILEB + 64;
+  static size_t smem(int T) { return 2 * (size_t)T * ROWB + 64; }
 };
 
-template <typename R, int BT, int RPT>
+// ntb = log2(threads per CTA) in 6..8; a CTA owns T = RPT << ntb rows.
+template <typename R, int BT>
 __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* __restrict__ groups, int ngroups,
-                                                     const typename CT<R>::T* __restrict__ psi,
+                                                     int ntb, const typename CT<R>::T* __restrict__ psi,
                                                      typename CT<R>::T* __restrict__ y) {
-  using Cfg = TileCfg<R, BT, RPT>;
+  using Cfg = TileCfg<R, BT>;
   using C = typename CT<R>::T;
   using S = typename std::conditional<Cfg::CH == 0, C, typename Slot<R>::T>::type;
-  constexpr int NT = Cfg::NT, T = Cfg::T, ROWB = Cfg::ROWB, TILEB = Cfg::TILEB, CH = Cfg::CH, NS = Cfg::NS;
+  constexpr int RPT = Cfg::RPT, ROWB = Cfg::ROWB, CH = Cfg::CH, NS = Cfg::NS;
+  const int NT = 1 << ntb, T = RPT << ntb, TILEB = T * ROWB;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * TILEB);
   const C* __restrict__ t4 = static_cast<const C*>(p.m4_tab);
@@ -261,7 +270,12 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t tile = blockIdx.x;
   const int n = p.n;
+  // lane-rotated chunk order: lanes reading the same slot of different rows hit distinct banks
   const int rho = CH >= 8 ? (lane & 7) : (CH >= 2 ? ((lane * CH / 8) % CH) : 0);
+  uint32_t soff[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) soff[k] = CH ? (uint32_t)(((k + rho) & (CH - 1)) * 16) : 0u;
+  const int fsh = 5 * (ntb - 6);  // flip patterns of row bits ntb, ntb+1, ntb+2
   uint32_t xf[RPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
@@ -283,9 +297,9 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       const C v = reinterpret_cast<const C*>(tb)[sr];
       cmac(a[0], cr, ci, v);
     } else {
-      const S* row = reinterpret_cast<const S*>(tb + (size_t)sr * ROWB);
+      const unsigned char* row = tb + (size_t)sr * ROWB;
 #pragma unroll
-      for (int k = 0; k < NS; ++k) Slot<R>::mac(a[k], cr, ci, row[(k + rho) & (CH - 1)]);
+      for (int k = 0; k < NS; ++k) Slot<R>::mac(a[k], cr, ci, *reinterpret_cast<const S*>(row + soff[k]));
     }
   };
 
@@ -300,8 +314,8 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     if (tid == 0) {
       const int b = g & 1;
       const uint32_t part = tile ^ (uint32_t)__ldg(&groups[g].x);
-      tma::expect_tx(&bar[b], TILEB);
-      tma::bulk_load(sm + b * TILEB, src + (size_t)part * TILEB, TILEB, &bar[b]);
+      tma::expect_tx(&bar[b], (uint32_t)TILEB);
+      tma::bulk_load(sm + b * TILEB, src + (size_t)part * TILEB, (uint32_t)TILEB, &bar[b]);
     }
   };
   issue(0);
@@ -317,17 +331,15 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       for (int k = gr.y; k < gr.z; ++k) {
         const uint4 rec = __ldg(&p.m4_rec[k]);
         const uint32_t lo = rec.x & (uint32_t)(T - 1);
-        const uint32_t s = rec.z, x0 = xf[0];
-        const uint32_t u = ((x0 >> (s & 0xffu)) & 1u) | (((x0 >> ((s >> 8) & 0xffu)) & 1u) << 1) |
-                           (((x0 >> ((s >> 16) & 0xffu)) & 1u) << 2) | (((x0 >> (s >> 24)) & 1u) << 3);
-        const uint32_t idx0 = u | ((__popc(rec.y & x0) & 1u) << 4);
+        const uint32_t idx0 = supp_bits(xf[0], rec.z) | ((__popc(rec.y & xf[0]) & 1u) << 4);
+        const uint32_t fl = rec.w >> fsh;
         const C* tab = t4 + (size_t)k * 32;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           uint32_t idx = idx0;
-          if (i & 1) idx ^= rec.w & 31u;
-          if (i & 2) idx ^= (rec.w >> 5) & 31u;
-          if (i & 4) idx ^= (rec.w >> 10) & 31u;
+          if (i & 1) idx ^= fl & 31u;
+          if (i & 2) idx ^= (fl >> 5) & 31u;
+          if (i & 4) idx ^= (fl >> 10) & 31u;
           const C cf = __ldg(&tab[idx]);
           mac_row(acc[i], cf.x, cf.y, tb, (uint32_t)(tid + i * NT) ^ lo);
         }
@@ -374,19 +386,24 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     if constexpr (CH == 0) {
       reinterpret_cast<C*>(dst)[row] = acc[i][0];
     } else {
-      S* out = reinterpret_cast<S*>(dst + row * ROWB);
+      unsigned char* out = dst + row * ROWB;
 #pragma unroll
-      for (int k = 0; k < NS; ++k) out[(k + rho) & (CH - 1)] = acc[i][k];
+      for (int k = 0; k < NS; ++k) *reinterpret_cast<S*>(out + soff[k]) = acc[i][k];
     }
   }
 }
 
-template <typename R, int BT, int RPT>
+template <typename R, int BT>
 int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st) {
-  using Cfg = TileCfg<R, BT, RPT>;
+  using Cfg = TileCfg<R, BT>;
   using C = typename CT<R>::T;
+  // widest CTA that still gives >= 2 CTAs per SM; narrower CTAs for small sectors
+  int ntb = 8;
+  while (ntb > 6 && p.D / ((int64_t)Cfg::RPT << ntb) < 2 * 152) --ntb;
+  const int T = Cfg::RPT << ntb;
+  if (p.D < T) return 1;
   int tb = 0;
-  while ((1 << tb) < Cfg::T) ++tb;
+  while ((1 << tb) < T) ++tb;
   const int4* groups = nullptr;
   int ng = 0;
   if (p.no_alloc) {
@@ -394,15 +411,16 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   } else {
     SYK_TRY(tile_groups(p.terms, tb, &groups, &ng));
   }
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Cfg::SMEM));
-    attr_set = true;
+  const size_t smem = Cfg::smem(T);
+  static size_t attr_set = 0;  // per instantiation: largest dynamic smem enabled so far
+  if (smem > attr_set) {
+    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Cfg::smem(Cfg::RPT << 8)));
+    attr_set = Cfg::smem(Cfg::RPT << 8);
   }
-  const unsigned blocks = (unsigned)(p.D / Cfg::T);
-  k_apply_tiled<R, BT, RPT><<<blocks, Cfg::NT, Cfg::SMEM, st>>>(p, groups, ng, static_cast<const C*>(psi),
-                                                                 static_cast<C*>(y));
+  const unsigned blocks = (unsigned)(p.D / T);
+  k_apply_tiled<R, BT><<<blocks, 1 << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
+                                                       static_cast<C*>(y));
   count_launch();
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
@@ -412,26 +430,13 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
 template <typename R>
 int try_tiled(const ApplyParams& p, const void* psi, void* y, int64_t batch, cudaStream_t st) {
   if ((reinterpret_cast<uintptr_t>(psi) & 15) || (reinterpret_cast<uintptr_t>(y) & 15)) return 1;
-  constexpr bool F = sizeof(R) == 4;
-  auto fits = [&](int T) { return p.D >= T; };
   switch (batch) {
-    case 1:
-      if (!fits(F ? 2048 : 1024)) return 1;
-      return F ? launch_tiled<R, 1, 8>(p, psi, y, st) : launch_tiled<R, 1, 4>(p, psi, y, st);
-    case 2:
-      if (!fits(F ? 1024 : 512)) return 1;
-      return F ? launch_tiled<R, 2, 4>(p, psi, y, st) : launch_tiled<R, 2, 2>(p, psi, y, st);
-    case 4:
-      if (!fits(F ? 1024 : 512)) return 1;
-      return F ? launch_tiled<R, 4, 4>(p, psi, y, st) : launch_tiled<R, 4, 2>(p, psi, y, st);
-    case 8:
-      if (!fits(F ? 512 : 256)) return 1;
-      return F ? launch_tiled<R, 8, 2>(p, psi, y, st) : launch_tiled<R, 8, 1>(p, psi, y, st);
-    case 16:
-      if (!fits(F ? 512 : 256)) return 1;
-      return F ? launch_tiled<R, 16, 2>(p, psi, y, st) : launch_tiled<R, 16, 1>(p, psi, y, st);
-    default:
-      return 1;
+    case 1: return launch_tiled<R, 1>(p, psi, y, st);
+    case 2: return launch_tiled<R, 2>(p, psi, y, st);
+    case 4: return launch_tiled<R, 4>(p, psi, y, st);
+    case 8: return launch_tiled<R, 8>(p, psi, y, st);
+    case 16: return launch_tiled<R, 16>(p, psi, y, st);
+    default: return 1;
   }
 }
 

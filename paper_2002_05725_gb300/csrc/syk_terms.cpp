@@ -183,12 +183,15 @@ extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
           if ((m >> k) & 1) pos[o++] = k;
         r.mc = uint32_t(m & Dmask);
         r.zeta = uint32_t(zeta0);
-        r.supp = uint32_t(pos[0]) | uint32_t(pos[1]) << 8 | uint32_t(pos[2]) << 16 | uint32_t(pos[3]) << 24;
-        // Table-index change when compact row bit j flips (j = 8, 9, 10): bit j of the full
-        // index flips and so does the top bit n-1 (the parity of the compact index).
+        // support bit k of the full index lands on bit k of the table index after a right
+        // shift by pos[k] - k (pos is ascending, so every shift is >= 0)
+        r.supp = uint32_t(pos[0]) | uint32_t(pos[1] - 1) << 8 | uint32_t(pos[2] - 2) << 16 |
+                 uint32_t(pos[3] - 3) << 24;
+        // Table-index change when compact row bit j flips (j = 6..10): bit j of the full index
+        // flips and so does the top bit n-1 (the parity of the compact index).
         const int top = n - 1;
-        for (int b = 0; b < 3; ++b) {
-          const int j = 8 + b;
+        for (int b = 0; b < 5; ++b) {
+          const int j = 6 + b;
           uint32_t f = 0;
           if (j < top) {
             for (int k = 0; k < 4; ++k)
