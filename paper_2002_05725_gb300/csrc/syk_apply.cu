@@ -250,7 +250,13 @@ struct TileCfg {
   static constexpr int ROWB = BT * (int)sizeof(C);
   static constexpr int CH = ROWB >= 16 ? ROWB / 16 : 0;  // 16-byte chunks per row
   static constexpr int NS = CH ? CH : 1;
-  static size_t smem(int T) { return 2 * (size_t)T * ROWB + 64; }
+  // each buffer stages the partner tile plus the records and 32-entry coefficient
+  // tables of up to GMAX popcount-4 masks
+  static constexpr int GMAX = 16;
+  static constexpr int TABB = 32 * (int)sizeof(C);
+  static constexpr int AUXB = GMAX * (TABB + 16);
+  static size_t buf_bytes(int T) { return (size_t)T * ROWB + AUXB; }
+  static size_t smem(int T) { return 2 * buf_bytes(T) + 64; }
 };
 
 // ntb = log2(threads per CTA) in 6..8; a CTA owns T = RPT << ntb rows.
@@ -262,9 +268,10 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   using C = typename CT<R>::T;
   using S = typename std::conditional<Cfg::CH == 0, C, typename Slot<R>::T>::type;
   constexpr int RPT = Cfg::RPT, ROWB = Cfg::ROWB, CH = Cfg::CH, NS = Cfg::NS;
-  const int NT = 1 << ntb, T = RPT << ntb, TILEB = T * ROWB;
+  constexpr int GMAX = Cfg::GMAX, TABB = Cfg::TABB;
+  const int NT = 1 << ntb, T = RPT << ntb, TILEB = T * ROWB, BUFB = TILEB + Cfg::AUXB;
   extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * TILEB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * BUFB);
   const C* __restrict__ t4 = static_cast<const C*>(p.m4_tab);
   const C* __restrict__ t2 = static_cast<const C*>(p.m2_tab);
   const int tid = threadIdx.x, lane = tid & 31;
@@ -310,12 +317,20 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   }
   __syncthreads();
   const unsigned char* src = reinterpret_cast<const unsigned char*>(psi);
+  // one transaction per chunk: partner tile psi[tile ^ h], then the chunk's tables and records
   auto issue = [&](int g) {
     if (tid == 0) {
       const int b = g & 1;
-      const uint32_t part = tile ^ (uint32_t)__ldg(&groups[g].x);
-      tma::expect_tx(&bar[b], (uint32_t)TILEB);
-      tma::bulk_load(sm + b * TILEB, src + (size_t)part * TILEB, (uint32_t)TILEB, &bar[b]);
+      const int4 gr = __ldg(&groups[g]);
+      const uint32_t part = tile ^ ((uint32_t)gr.x & 0x7fffffffu);
+      const uint32_t nm = (uint32_t)(gr.z - gr.y);
+      unsigned char* buf = sm + b * BUFB;
+      tma::expect_tx(&bar[b], (uint32_t)TILEB + nm * (uint32_t)(TABB + 16));
+      tma::bulk_load(buf, src + (size_t)part * TILEB, (uint32_t)TILEB, &bar[b]);
+      if (nm) {
+        tma::bulk_load(buf + TILEB, t4 + (size_t)gr.y * 32, nm * TABB, &bar[b]);
+        tma::bulk_load(buf + TILEB + GMAX * TABB, p.m4_rec + gr.y, nm * 16u, &bar[b]);
+      }
     }
   };
   issue(0);
@@ -325,22 +340,25 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     if (g + 1 < ngroups) issue(g + 1);
     const bool ok = tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
     const int4 gr = __ldg(&groups[g]);
-    const unsigned char* tb = sm + (g & 1) * TILEB;
+    const unsigned char* tb = sm + (g & 1) * BUFB;
     if (ok) {
-      // popcount-4 masks of this group
-      for (int k = gr.y; k < gr.z; ++k) {
-        const uint4 rec = __ldg(&p.m4_rec[k]);
+      // popcount-4 masks of this chunk: records and tables are in shared memory
+      const C* stab = reinterpret_cast<const C*>(tb + TILEB);
+      const uint4* srec = reinterpret_cast<const uint4*>(tb + TILEB + GMAX * TABB);
+      const int nm = gr.z - gr.y;
+      for (int kk = 0; kk < nm; ++kk) {
+        const uint4 rec = srec[kk];
         const uint32_t lo = rec.x & (uint32_t)(T - 1);
         const uint32_t idx0 = supp_bits(xf[0], rec.z) | ((__popc(rec.y & xf[0]) & 1u) << 4);
         const uint32_t fl = rec.w >> fsh;
-        const C* tab = t4 + (size_t)k * 32;
+        const C* tab = stab + kk * 32;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           uint32_t idx = idx0;
           if (i & 1) idx ^= fl & 31u;
           if (i & 2) idx ^= (fl >> 5) & 31u;
           if (i & 4) idx ^= (fl >> 10) & 31u;
-          const C cf = __ldg(&tab[idx]);
+          const C cf = tab[idx];
           mac_row(acc[i], cf.x, cf.y, tb, (uint32_t)(tid + i * NT) ^ lo);
         }
       }
@@ -356,8 +374,8 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
           mac_row(acc[i], cr, ci, tb, (uint32_t)(tid + i * NT) ^ lo);
         }
       }
-      // diagonal (the own tile is the group with h = 0)
-      if (gr.x == 0) {
+      // diagonal (the own tile: first chunk of h = 0)
+      if ((uint32_t)gr.x == 0x80000000u) {
 #pragma unroll
         for (int i = 0; i < RPT; ++i)
           mac_row(acc[i], diag_coef<R>(static_cast<const R*>(p.wd), n, xf[i]), R(0), tb, (uint32_t)(tid + i * NT));
@@ -407,9 +425,9 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   const int4* groups = nullptr;
   int ng = 0;
   if (p.no_alloc) {
-    if (!tile_groups_cached(p.terms, tb, &groups, &ng)) return 1;  // row kernel instead
+    if (!tile_groups_cached(p.terms, tb, Cfg::GMAX, &groups, &ng)) return 1;  // row kernel instead
   } else {
-    SYK_TRY(tile_groups(p.terms, tb, &groups, &ng));
+    SYK_TRY(tile_groups(p.terms, tb, Cfg::GMAX, &groups, &ng));
   }
   const size_t smem = Cfg::smem(T);
   static size_t attr_set = 0;  // per instantiation: largest dynamic smem enabled so far

@@ -61,11 +61,13 @@ struct ApplyParams {
   bool no_alloc;           // host-side: never allocate (use only cached tile-group lists)
 };
 
-// Groups of X-masks sharing the compact-mask bits above a tile of 2^tb rows:
-// {h, first popcount-4 mask, end, first popcount-2 mask | end << 16}.
-int tile_groups(const syk_terms* t, int tb, const int4** dev, int* count);
-// Lookup only: returns false if the list for tb has not been built on this device yet.
-bool tile_groups_cached(const syk_terms* t, int tb, const int4** dev, int* count);
+// Chunks of X-masks sharing the compact-mask bits h above a tile of 2^tb rows, at
+// most gmax popcount-4 masks per chunk: {h | first-chunk-of-h << 31, first
+// popcount-4 mask, end, first popcount-2 mask | end << 16} (popcount-2 masks and
+// the diagonal go with the first chunk of their h).
+int tile_groups(const syk_terms* t, int tb, int gmax, const int4** dev, int* count);
+// Lookup only: returns false if that list has not been built on this device yet.
+bool tile_groups_cached(const syk_terms* t, int tb, int gmax, const int4** dev, int* count);
 
 int ensure_device_tables(const syk_terms* t);
 int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p);

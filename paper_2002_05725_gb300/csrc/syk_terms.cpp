@@ -378,19 +378,19 @@ int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p)
   return SYK_OK;
 }
 
-bool tile_groups_cached(const syk_terms* t, int tb, const int4** out, int* count) {
+bool tile_groups_cached(const syk_terms* t, int tb, int gmax, const int4** out, int* count) {
   std::lock_guard<std::mutex> lock(t->mtx);
-  auto it = t->groups_dev.find(tb);
+  auto it = t->groups_dev.find(tb << 16 | gmax);
   if (it == t->groups_dev.end()) return false;
   *out = it->second.first;
   *count = it->second.second;
   return true;
 }
-
-int tile_groups(const syk_terms* t, int tb, const int4** out, int* count) {
+int tile_groups(const syk_terms* t, int tb, int gmax, const int4** out, int* count) {
   SYK_TRY(ensure_device_tables(t));
   std::lock_guard<std::mutex> lock(t->mtx);
-  auto it = t->groups_dev.find(tb);
+  const int key = tb << 16 | gmax;
+  auto it = t->groups_dev.find(key);
   if (it == t->groups_dev.end()) {
     std::vector<int4> g;
     size_t i4 = 0, i2 = 0;
@@ -405,12 +405,20 @@ int tile_groups(const syk_terms* t, int tb, const int4** out, int* count) {
       while (i4 < n4 && (t->m4_rec[4 * i4] >> tb) == h) ++i4;
       while (i2 < n2 && (t->m2_rec[4 * i2] >> tb) == h) ++i2;
       if (h == 0) diag = true;
-      g.push_back(make_int4(int(h), int(b4), int(i4), int(b2 | (i2 << 16))));
+      size_t c0 = b4;
+      bool first = true;
+      do {
+        const size_t c1 = std::min(i4, c0 + size_t(gmax));
+        const int k2 = first ? int(b2 | (i2 << 16)) : 0;
+        g.push_back(make_int4(int(h | (first ? 0x80000000u : 0u)), int(c0), int(c1), k2));
+        first = false;
+        c0 = c1;
+      } while (c0 < i4);
     }
     int4* d = nullptr;
     SYK_CUDA_CHECK(cudaMalloc(&d, g.size() * sizeof(int4)));
     SYK_CUDA_CHECK(cudaMemcpy(d, g.data(), g.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    it = t->groups_dev.emplace(tb, std::make_pair(d, int(g.size()))).first;
+    it = t->groups_dev.emplace(key, std::make_pair(d, int(g.size()))).first;
   }
   *out = it->second.first;
   *count = it->second.second;
