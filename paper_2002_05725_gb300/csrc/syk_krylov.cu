@@ -80,33 +80,48 @@ __device__ double2 block_reduce_cols(double2 v, int B, double2* sm) {
   return r;
 }
 
-// part[(k*G + g)*B + b] = sum over this block's elements of conj(V_k) w
+// part[(k*G + g)*B + b] = sum over this block's elements of conj(V_k) w, for
+// k in [KC*blockIdx.y, min(nk, KC*(blockIdx.y+1))): w is read once per KC vectors.
+constexpr int KC = 8;
 template <typename R>
-__global__ void k_dots(int nk0, const typename CT<R>::T* __restrict__ V, size_t vs,
+__global__ void k_dots(int nk, const typename CT<R>::T* __restrict__ V, size_t vs,
                        const typename CT<R>::T* __restrict__ w, int64_t total, int B, double2* __restrict__ part) {
   extern __shared__ double2 sm[];
-  const int k = nk0 + blockIdx.y;
-  const typename CT<R>::T* __restrict__ v = V + (size_t)k * vs;
-  DotAcc<R> acc;
+  const int k0 = KC * blockIdx.y;
+  const int kc = min(KC, nk - k0);
+  DotAcc<R> acc[KC];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    acc.add(v[e], w[e]);
-    acc.tick();
+    const typename CT<R>::T we = w[e];
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+      if (j < kc) {
+        acc[j].add(V[(size_t)(k0 + j) * vs + e], we);
+        acc[j].tick();
+      }
   }
-  double2 r = block_reduce_cols(acc.get(), B, sm);
-  if ((int)threadIdx.x < B) part[((size_t)k * gridDim.x + blockIdx.x) * B + threadIdx.x] = r;
+  for (int j = 0; j < kc; ++j) {
+    double2 r = block_reduce_cols(acc[j].get(), B, sm);
+    if ((int)threadIdx.x < B) part[((size_t)(k0 + j) * gridDim.x + blockIdx.x) * B + threadIdx.x] = r;
+  }
 }
 
+// out[k*B + b] = sum_g part[(k*G + g)*B + b]; one warp per (k, b), deterministic order
 __global__ void k_reduce_parts(int nk, int G, int B, const double2* __restrict__ part, double2* __restrict__ out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (idx >= nk * B) return;
   const int k = idx / B, b = idx - k * B;
-  double2 s = make_double2(0.0, 0.0);
-  for (int g = 0; g < G; ++g) {
+  double sx = 0.0, sy = 0.0;
+  for (int g = lane; g < G; g += 32) {
     const double2 p = part[((size_t)k * G + g) * B + b];
-    s.x += p.x;
-    s.y += p.y;
+    sx += p.x;
+    sy += p.y;
   }
-  out[idx] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if (lane == 0) out[idx] = make_double2(sx, sy);
 }
 
 // w -= sum_{k<nk} h_k V_k (per column); npart[g*B + b] = partial |w|^2 of the result
@@ -374,9 +389,9 @@ __global__ void k_tridiag_coef(int m, int B, const double* __restrict__ theta, c
 template <typename R>
 struct Ops {
   using C = typename CT<R>::T;
-  static void dots(const KrylovWS& ws, int k0, int nk, const void* V, size_t vs, const void* w, cudaStream_t st) {
-    dim3 grid(ws.G, nk);
-    k_dots<R><<<grid, ws.bdim, ws.bdim * sizeof(double2), st>>>(k0, (const C*)V, vs, (const C*)w, ws.D * ws.B,
+  static void dots(const KrylovWS& ws, int nk, const void* V, size_t vs, const void* w, cudaStream_t st) {
+    dim3 grid(ws.G, (nk + KC - 1) / KC);
+    k_dots<R><<<grid, ws.bdim, ws.bdim * sizeof(double2), st>>>(nk, (const C*)V, vs, (const C*)w, ws.D * ws.B,
                                                                  (int)ws.B, ws.part);
     count_launch();
   }
@@ -398,8 +413,8 @@ struct Ops {
 };
 
 void reduce_parts(const KrylovWS& ws, int nk, double2* out, cudaStream_t st) {
-  const int n = nk * (int)ws.B;
-  k_reduce_parts<<<(n + 127) / 128, 128, 0, st>>>(nk, ws.G, (int)ws.B, ws.part, out);
+  const int n = nk * (int)ws.B;  // one warp each
+  k_reduce_parts<<<(n + 7) / 8, 256, 0, st>>>(nk, ws.G, (int)ws.B, ws.part, out);
   count_launch();
 }
 
@@ -476,8 +491,8 @@ int dot_columns(const void* x, const void* y, int64_t D, int64_t B, int dtype, K
     set_error("dot_columns: workspace shape mismatch");
     return SYK_EINVAL;
   }
-  if (dtype == SYK_C64) Ops<float>::dots(ws, 0, 1, x, 0, y, st);
-  else Ops<double>::dots(ws, 0, 1, x, 0, y, st);
+  if (dtype == SYK_C64) Ops<float>::dots(ws, 1, x, 0, y, st);
+  else Ops<double>::dots(ws, 1, x, 0, y, st);
   reduce_parts(ws, 1, res, st);
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
@@ -506,7 +521,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
       return SYK_ENUMERIC;
     }
     // v_0 = cur / ||cur||
-    Ops<R>::dots(ws, 0, 1, cur, 0, cur, st);
+    Ops<R>::dots(ws, 1, cur, 0, cur, st);
     reduce_parts(ws, 1, ws.h1, st);
     k_norm_init<<<(int(B) + 127) / 128, 128, 0, st>>>(int(B), ws.h1, ws.beta0, ws.inv, ws.status);
     count_launch();
@@ -515,11 +530,11 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
     for (int j = 0; j < m; ++j) {
       SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, B, st));
       // first Gram-Schmidt pass
-      Ops<R>::dots(ws, 0, j + 1, ws.V, vs, ws.w, st);
+      Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
       reduce_parts(ws, j + 1, ws.h1, st);
       Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, nullptr, st);
       // second pass
-      Ops<R>::dots(ws, 0, j + 1, ws.V, vs, ws.w, st);
+      Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
       reduce_parts(ws, j + 1, ws.h2, st);
       Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
       k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, ws.h2, ws.npart, ws.alpha,
