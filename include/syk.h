@@ -101,7 +101,8 @@ int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const double* be
 size_t syk_workspace_bytes(int N, int dtype, int krylov_dim, int64_t batch, int kind);
 
 /* syk_expmv -- out = e^{z H} psi in sector `parity` by Lanczos with full
- * (two-pass classical Gram-Schmidt) reorthogonalisation (Supp. Sec. I.B;
+ * classical Gram-Schmidt reorthogonalisation against the whole basis (two
+ * passes for SYK_C128, one for SYK_C64) (Supp. Sec. I.B;
  * Saad 1992 a-posteriori error estimate).  z = z_re + i z_im: z = -i t for
  * real time, z = -tau for imaginary time.  Each Krylov basis of dimension
  * <= krylov_dim (2..SYK_MAX_KRYLOV) advances all states of the batch by a

@@ -20,7 +20,9 @@
 // the thread index (bits 6..10 depending on the CTA width); the table index of a
 // popcount-4 mask for those rows follows from the first row's by XOR with
 // per-mask flip patterns, so the bit extraction is done once per mask.  Small
-// sectors use narrower CTAs (64 or 128 threads) so that the grid fills the SMs.  Rows wider than 16 bytes are read in 16-byte chunks in a lane-rotated
+// sectors or single states would leave SMs idle, so the mask chunks of one tile are
+// then split round-robin over a thread-block cluster of up to 8 CTAs, whose
+// partial sums are reduced in a fixed order through distributed shared memory.  Rows wider than 16 bytes are read in 16-byte chunks in a lane-rotated
 // order so that the 32 lanes of a warp hit distinct shared-memory banks.
 // k_apply_rows (fallback: any batch, any alignment, small sectors): one thread
 // per row, gathers straight from global memory.
@@ -178,6 +180,39 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity) {
     if (try_wait(b, parity)) return true;
   return false;
 }
+// thread-block cluster helpers
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared-memory address of the same offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr_local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr_local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float4 ld_cluster(uint32_t a, float4) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ double2 ld_cluster(uint32_t a, double2) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+  return v;
+}
 }  // namespace tma
 
 template <typename R>
@@ -275,7 +310,10 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   const C* __restrict__ t4 = static_cast<const C*>(p.m4_tab);
   const C* __restrict__ t2 = static_cast<const C*>(p.m2_tab);
   const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t tile = blockIdx.x;
+  // the CTAs of a cluster share one tile and split its mask chunks round-robin
+  const uint32_t crank = tma::cluster_rank(), csize = tma::cluster_size();
+  const uint32_t tile = blockIdx.x / csize;
+  const int nmine = (int)crank < ngroups ? (ngroups - (int)crank + (int)csize - 1) / (int)csize : 0;
   const int n = p.n;
   // lane-rotated chunk order: lanes reading the same slot of different rows hit distinct banks
   const int rho = CH >= 8 ? (lane & 7) : (CH >= 2 ? ((lane * CH / 8) % CH) : 0);
@@ -318,10 +356,10 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   __syncthreads();
   const unsigned char* src = reinterpret_cast<const unsigned char*>(psi);
   // one transaction per chunk: partner tile psi[tile ^ h], then the chunk's tables and records
-  auto issue = [&](int g) {
+  auto issue = [&](int q) {
     if (tid == 0) {
-      const int b = g & 1;
-      const int4 gr = __ldg(&groups[g]);
+      const int b = q & 1;
+      const int4 gr = __ldg(&groups[(int)crank + q * (int)csize]);
       const uint32_t part = tile ^ ((uint32_t)gr.x & 0x7fffffffu);
       const uint32_t nm = (uint32_t)(gr.z - gr.y);
       unsigned char* buf = sm + b * BUFB;
@@ -333,13 +371,13 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       }
     }
   };
-  issue(0);
+  if (nmine > 0) issue(0);
   bool failed = false;
-  int g = 0;
-  for (; g < ngroups; ++g) {
-    if (g + 1 < ngroups) issue(g + 1);
+  int g = 0;  // index among this CTA's chunks
+  for (; g < nmine; ++g) {
+    if (g + 1 < nmine) issue(g + 1);
     const bool ok = tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
-    const int4 gr = __ldg(&groups[g]);
+    const int4 gr = __ldg(&groups[(int)crank + g * (int)csize]);
     const unsigned char* tb = sm + (g & 1) * BUFB;
     if (ok) {
       // popcount-4 masks of this chunk: records and tables are in shared memory
@@ -388,19 +426,19 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     }
   }
   if (failed) {
-    // drain: let any copy still in flight land before the CTA exits
+    // drain: let any copy still in flight land before the buffers are reused or the CTA exits
     if (tid == 0) {
       atomicOr(p.status, 4);
       tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
-      if (g + 1 < ngroups) tma::wait_bounded(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
+      if (g + 1 < nmine) tma::wait_bounded(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
     }
     __syncthreads();
-    return;
   }
-  unsigned char* dst = reinterpret_cast<unsigned char*>(y);
+  // rows are written in the natural layout (logical chunk k of a row at soff[k])
+  unsigned char* dst = csize == 1 ? reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB : sm;
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
-    const size_t row = (size_t)tile * T + (size_t)(tid + i * NT);
+    const size_t row = (size_t)(tid + i * NT);
     if constexpr (CH == 0) {
       reinterpret_cast<C*>(dst)[row] = acc[i][0];
     } else {
@@ -409,17 +447,43 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       for (int k = 0; k < NS; ++k) *reinterpret_cast<S*>(out + soff[k]) = acc[i][k];
     }
   }
+  if (csize > 1) {
+    // every CTA of the cluster reduces 1/csize of the tile's rows over the partial sums
+    // held in the cluster's shared memories (fixed rank order: deterministic)
+    using V16 = typename Slot<R>::T;
+    tma::cluster_sync();
+    const int units = TILEB / 16 / (int)csize;
+    const uint32_t base = tma::saddr(sm) + crank * (uint32_t)units * 16u;
+    unsigned char* yt = reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB + (size_t)crank * units * 16;
+    for (int u = tid; u < units; u += NT) {
+      V16 sum = tma::ld_cluster(tma::map_rank(base + 16u * u, 0), V16{});
+      for (uint32_t r = 1; r < csize; ++r) {
+        const V16 v = tma::ld_cluster(tma::map_rank(base + 16u * u, r), V16{});
+        if constexpr (sizeof(R) == 4) {
+          sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+        } else {
+          sum.x += v.x; sum.y += v.y;
+        }
+      }
+      *reinterpret_cast<V16*>(yt + 16u * u) = sum;
+    }
+    tma::cluster_sync();  // no CTA leaves while others still read its shared memory
+  }
 }
 
 template <typename R, int BT>
 int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st) {
   using Cfg = TileCfg<R, BT>;
   using C = typename CT<R>::T;
-  // widest CTA that still gives >= 2 CTAs per SM; narrower CTAs for small sectors
+  // 256-thread CTAs (narrower only if the sector is smaller than a tile); if the grid
+  // has too few warps, the mask chunks of a tile are split across a cluster of CTAs
   int ntb = 8;
-  while (ntb > 6 && p.D / ((int64_t)Cfg::RPT << ntb) < 2 * 152) --ntb;
+  while (ntb > 6 && p.D < ((int64_t)Cfg::RPT << ntb)) --ntb;
   const int T = Cfg::RPT << ntb;
   if (p.D < T) return 1;
+  const int64_t ntiles = p.D / T;
+  int cs = 1;
+  while (cs < 8 && ntiles * cs * ((1 << ntb) / 32) < 152 * 32) cs *= 2;
   int tb = 0;
   while ((1 << tb) < T) ++tb;
   const int4* groups = nullptr;
@@ -436,9 +500,20 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
                                         (int)Cfg::smem(Cfg::RPT << 8)));
     attr_set = Cfg::smem(Cfg::RPT << 8);
   }
-  const unsigned blocks = (unsigned)(p.D / T);
-  k_apply_tiled<R, BT><<<blocks, 1 << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
-                                                       static_cast<C*>(y));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ntiles * cs), 1, 1);
+  cfg.blockDim = dim3(1u << ntb, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SYK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_apply_tiled<R, BT>, p, groups, ng, ntb, static_cast<const C*>(psi),
+                                    static_cast<C*>(y)));
   count_launch();
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;

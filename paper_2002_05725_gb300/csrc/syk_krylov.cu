@@ -1,5 +1,5 @@
-// Krylov expmv (Supp. Sec. I.B): Lanczos basis with two-pass classical
-// Gram-Schmidt reorthogonalisation (K2 + K7), eigendecomposition of the FP64
+// Krylov expmv (Supp. Sec. I.B): Lanczos basis with full classical Gram-Schmidt
+// reorthogonalisation (two passes for complex128, one for complex64) (K2 + K7), eigendecomposition of the FP64
 // tridiagonal projection and its exponential (K3), and the combination
 // psi_out = V c (K4).  All scalars are FP64; complex64 vectors use FP32
 // arithmetic with FP64 accumulation of every reduction.
@@ -194,7 +194,7 @@ __global__ void k_lanczos_scalars(int j, int B, int G, const double2* __restrict
                                   double* __restrict__ beta, double* __restrict__ inv, int* status, double bt) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  const double a = h1[j * B + b].x + h2[j * B + b].x;
+  const double a = h1[j * B + b].x + (h2 ? h2[j * B + b].x : 0.0);
   double n2 = 0.0;
   for (int g = 0; g < G; ++g) n2 += npart[(size_t)g * B + b];
   double be = sqrt(fmax(n2, 0.0));
@@ -508,6 +508,9 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
   const size_t vs = size_t(ws.D) * B;
   const int m = ws.m;
   const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
+  // complex64 vectors carry ~1e-7 relative error, which one reorthogonalisation pass already
+  // reaches; complex128 vectors get the second pass ("twice is enough")
+  const bool two_pass = dtype == SYK_C128;
   const double zr = z.real(), zi = z.imag();
   int* hstat = static_cast<int*>(ws.host_stage ? ws.host_stage : pinned_scratch(64));
   double* hs = reinterpret_cast<double*>(hstat + 4);
@@ -529,16 +532,17 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
     int m_eff = m;
     for (int j = 0; j < m; ++j) {
       SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, B, st));
-      // first Gram-Schmidt pass
+      // classical Gram-Schmidt against the whole basis; a second pass for FP64 vectors
       Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
       reduce_parts(ws, j + 1, ws.h1, st);
-      Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, nullptr, st);
-      // second pass
-      Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
-      reduce_parts(ws, j + 1, ws.h2, st);
-      Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
-      k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, ws.h2, ws.npart, ws.alpha,
-                                                               ws.beta, ws.inv, ws.status, bt);
+      Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, two_pass ? nullptr : ws.npart, st);
+      if (two_pass) {
+        Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
+        reduce_parts(ws, j + 1, ws.h2, st);
+        Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
+      }
+      k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, two_pass ? ws.h2 : nullptr,
+                                                               ws.npart, ws.alpha, ws.beta, ws.inv, ws.status, bt);
       count_launch();
       if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
       const bool last = (j + 1 == m);
