@@ -168,6 +168,23 @@ int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t,
              const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
              double* F_re_im, void* stream);
 
+/* ------------------------------------------------------------- autotuner
+ * syk_autotune_apply -- times every tile configuration of the tiled matvec
+ * (CTA width 64/128/256 threads x thread-block cluster of 1/2/4/8 CTAs sharing a
+ * tile) for this term set's N, `dtype` and `batch` (1, 2, 4, 8 or 16) on
+ * scratch vectors it allocates, with `reps` timed applies each, and records
+ * the fastest; later syk_apply_H / syk_expmv calls with the same (N, dtype,
+ * batch) use it.  *best_ms (may be NULL) receives its time per apply.
+ * Synchronises `stream`.  The work of the batched workload has no counterpart
+ * in the paper; this only picks launch shapes. */
+int syk_autotune_apply(const syk_terms* terms, int parity, int dtype, int64_t batch, int reps,
+                       void* stream, double* best_ms);
+/* syk_autotune_export / _import -- the tuned table as JSON
+ * ({"apply_tiles": [{"N":..,"dtype":..,"batch":..,"ntb":..,"cluster":..,"ms":..}]}),
+ * so a tuning run can be cached in a file and reloaded. */
+int syk_autotune_export(char* buf, size_t len);
+int syk_autotune_import(const char* json);
+
 /* ------------------------------------------------------------- diagnostics
  * syk_last_error -- message of the last failed call on this thread ("" if none). */
 const char* syk_last_error(void);

@@ -29,6 +29,11 @@
 #include <cuda_runtime.h>
 
 #include <type_traits>
+#include <map>
+#include <mutex>
+#include <string>
+#include <cstdio>
+#include <cstring>
 
 #include <algorithm>
 #include <vector>
@@ -37,6 +42,30 @@
 #include "syk_internal.h"
 
 namespace syk {
+
+// Tile configuration chosen by the autotuner per (N, dtype, batch): CTA width 2^ntb and
+// cluster size cs.  Absent entries use the built-in heuristic.
+struct TileChoice {
+  int ntb, cs;
+  double ms;
+};
+static std::mutex g_tune_mtx;
+static std::map<uint64_t, TileChoice> g_tune;
+static uint64_t tune_key(int N, int dtype, int64_t batch) {
+  return (uint64_t)N | ((uint64_t)dtype << 8) | ((uint64_t)batch << 16);
+}
+static bool tile_choice_lookup(int N, int dtype, int64_t batch, TileChoice* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mtx);
+  auto it = g_tune.find(tune_key(N, dtype, batch));
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+static void tile_choice_set(int N, int dtype, int64_t batch, TileChoice c) {
+  std::lock_guard<std::mutex> lk(g_tune_mtx);
+  g_tune[tune_key(N, dtype, batch)] = c;
+}
+
 namespace {
 
 // Table index bits of a popcount-4 mask: bit k = bit pos_k of the full index xf.
@@ -475,15 +504,21 @@ template <typename R, int BT>
 int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st) {
   using Cfg = TileCfg<R, BT>;
   using C = typename CT<R>::T;
-  // 256-thread CTAs (narrower only if the sector is smaller than a tile); if the grid
-  // has too few warps, the mask chunks of a tile are split across a cluster of CTAs
-  int ntb = 8;
-  while (ntb > 6 && p.D < ((int64_t)Cfg::RPT << ntb)) --ntb;
+  int ntb = 8, cs = 1;
+  TileChoice tc;
+  if (tile_choice_lookup(p.n * 2, sizeof(R) == 4 ? SYK_C64 : SYK_C128, BT, &tc) && (Cfg::RPT << tc.ntb) <= p.D) {
+    ntb = tc.ntb;  // autotuned
+    cs = tc.cs;
+  } else {
+    // 256-thread CTAs (narrower only if the sector is smaller than a tile); if the grid
+    // has too few warps, the mask chunks of a tile are split across a cluster of CTAs
+    while (ntb > 6 && p.D < ((int64_t)Cfg::RPT << ntb)) --ntb;
+    const int64_t nt = p.D / ((int64_t)Cfg::RPT << ntb);
+    while (cs < 8 && nt * cs * ((1 << ntb) / 32) < 152 * 32) cs *= 2;
+  }
   const int T = Cfg::RPT << ntb;
   if (p.D < T) return 1;
   const int64_t ntiles = p.D / T;
-  int cs = 1;
-  while (cs < 8 && ntiles * cs * ((1 << ntb) / 32) < 152 * 32) cs *= 2;
   int tb = 0;
   while ((1 << tb) < T) ++tb;
   const int4* groups = nullptr;
@@ -499,6 +534,13 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)Cfg::smem(Cfg::RPT << 8)));
     attr_set = Cfg::smem(Cfg::RPT << 8);
+  }
+  if (cs == 1) {
+    k_apply_tiled<R, BT><<<(unsigned)ntiles, 1u << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
+                                                                     static_cast<C*>(y));
+    count_launch();
+    SYK_CUDA_CHECK(cudaGetLastError());
+    return SYK_OK;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ntiles * cs), 1, 1);
@@ -615,4 +657,137 @@ extern "C" int syk_apply_chi(int N, int i, int parity_in, int dtype, const void*
     return SYK_EINVAL;
   }
   return syk::launch_apply_chi(N, i, parity_in, dtype, psi, y, batch, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------- autotuner
+// Sweeps the tile configurations of the tiled matvec (CTA width 64/128/256 x cluster
+// size 1/2/4/8) for one (N, dtype, batch) on zero-filled scratch vectors, times each
+// with CUDA events on `stream` and records the fastest for later launches.
+extern "C" int syk_autotune_apply(const syk_terms* terms, int parity, int dtype, int64_t batch, int reps,
+                                  void* stream, double* best_ms) {
+  using namespace syk;
+  clear_error();
+  if (batch != 1 && batch != 2 && batch != 4 && batch != 8 && batch != 16) {
+    set_error("syk_autotune_apply: only batches of 1, 2, 4, 8 or 16 use the tiled matvec");
+    return SYK_EINVAL;
+  }
+  if (reps < 1) reps = 2;
+  ApplyParams P;
+  SYK_TRY(make_apply_params(terms, parity, dtype, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vb = size_t(P.D) * batch * dtype_size(dtype);
+  void *x = nullptr, *y = nullptr;
+  SYK_CUDA_CHECK(cudaMallocAsync(&x, vb, st));
+  cudaError_t e = cudaMallocAsync(&y, vb, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(x, st);
+    set_error("syk_autotune_apply: %s", cudaGetErrorString(e));
+    return SYK_ENOMEM;
+  }
+  cudaMemsetAsync(x, 0, vb, st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int N = terms->N;
+  const int rows_per_thread =
+      dtype == SYK_C64
+          ? (batch == 1 ? TileCfg<float, 1>::RPT : batch == 2 ? TileCfg<float, 2>::RPT : batch == 4 ? TileCfg<float, 4>::RPT
+             : batch == 8 ? TileCfg<float, 8>::RPT : TileCfg<float, 16>::RPT)
+          : (batch == 1 ? TileCfg<double, 1>::RPT : batch == 2 ? TileCfg<double, 2>::RPT
+             : batch == 4 ? TileCfg<double, 4>::RPT : batch == 8 ? TileCfg<double, 8>::RPT : TileCfg<double, 16>::RPT);
+  TileChoice best{0, 0, 1e300};
+  int rc = SYK_OK;
+  for (int ntb = 6; ntb <= 8 && rc == SYK_OK; ++ntb)
+    for (int cs = 1; cs <= 8 && rc == SYK_OK; cs *= 2) {
+      if ((int64_t(rows_per_thread) << ntb) > P.D) continue;  // tile larger than the sector
+      tile_choice_set(N, dtype, batch, TileChoice{ntb, cs, 0.0});
+      rc = launch_apply_H(P, dtype, x, y, batch, st);  // warm-up (also builds the chunk list)
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == SYK_OK; ++r) rc = launch_apply_H(P, dtype, x, y, batch, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = SYK_ECUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (rc == SYK_OK && ms < best.ms) best = TileChoice{ntb, cs, ms};
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(x, st);
+  cudaFreeAsync(y, st);
+  if (rc != SYK_OK || best.ntb == 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mtx);
+    g_tune.erase(tune_key(N, dtype, batch));
+    if (rc == SYK_OK) set_error("syk_autotune_apply: the sector is smaller than every tile");
+    return rc != SYK_OK ? rc : SYK_EINVAL;
+  }
+  tile_choice_set(N, dtype, batch, best);
+  if (best_ms) *best_ms = best.ms;
+  return SYK_OK;
+}
+
+// JSON form of the tuned table: {"apply_tiles": [{"N":40,"dtype":1,"batch":8,"ntb":8,"cluster":1,"ms":6.5}, ...]}
+extern "C" int syk_autotune_export(char* buf, size_t len) {
+  using namespace syk;
+  std::string js = "{\"apply_tiles\": [";
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mtx);
+    bool first = true;
+    for (auto& kv : g_tune) {
+      char item[160];
+      snprintf(item, sizeof(item), "%s{\"N\": %d, \"dtype\": %d, \"batch\": %d, \"ntb\": %d, \"cluster\": %d, \"ms\": %.6g}",
+               first ? "" : ", ", int(kv.first & 0xff), int((kv.first >> 8) & 0xff), int(kv.first >> 16),
+               kv.second.ntb, kv.second.cs, kv.second.ms);
+      js += item;
+      first = false;
+    }
+  }
+  js += "]}";
+  if (!buf || len < js.size() + 1) {
+    set_error("syk_autotune_export: buffer needs %zu bytes", js.size() + 1);
+    return SYK_EINVAL;
+  }
+  std::memcpy(buf, js.c_str(), js.size() + 1);
+  return SYK_OK;
+}
+
+// Reads entries written by syk_autotune_export (keys in any order; unknown keys ignored).
+extern "C" int syk_autotune_import(const char* json) {
+  using namespace syk;
+  if (!json) {
+    set_error("syk_autotune_import: NULL");
+    return SYK_EINVAL;
+  }
+  const char* p = std::strstr(json, "\"apply_tiles\"");
+  if (!p) {
+    set_error("syk_autotune_import: no apply_tiles array");
+    return SYK_EINVAL;
+  }
+  int count = 0;
+  while ((p = std::strchr(p, '{')) != nullptr) {
+    const char* end = std::strchr(p, '}');
+    if (!end) break;
+    std::string obj(p, end - p);
+    auto num = [&](const char* key, double* v) {
+      const std::string k = std::string("\"") + key + "\"";
+      size_t at = obj.find(k);
+      if (at == std::string::npos) return false;
+      at = obj.find(':', at);
+      if (at == std::string::npos) return false;
+      *v = std::strtod(obj.c_str() + at + 1, nullptr);
+      return true;
+    };
+    double N, dt, b, ntb, cs, ms = 0.0;
+    if (num("N", &N) && num("dtype", &dt) && num("batch", &b) && num("ntb", &ntb) && num("cluster", &cs)) {
+      num("ms", &ms);
+      if (ntb < 6 || ntb > 8 || (cs != 1 && cs != 2 && cs != 4 && cs != 8)) {
+        set_error("syk_autotune_import: invalid entry (ntb=%g cluster=%g)", ntb, cs);
+        return SYK_EINVAL;
+      }
+      tile_choice_set(int(N), int(dt), int64_t(b), TileChoice{int(ntb), int(cs), ms});
+      ++count;
+    }
+    p = end + 1;
+  }
+  return count > 0 ? SYK_OK : SYK_EINVAL;
 }

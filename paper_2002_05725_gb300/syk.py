@@ -60,6 +60,9 @@ def load(build_if_missing: bool = False):
         "syk_counters": (i32, [vp, vp, vp, i32]),
         "syk_profile_enable": (i32, [i32]),
         "syk_profile_read": (i32, [vp, vp, i32]),
+        "syk_autotune_apply": (i32, [vp, i32, i32, i64, i32, vp, vp]),
+        "syk_autotune_export": (i32, [ctypes.c_char_p, sz]),
+        "syk_autotune_import": (i32, [ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -73,7 +76,8 @@ def exported_symbols():
     """Names declared in include/syk.h that the loaded library must export."""
     return ["syk_build_terms", "syk_free_terms", "syk_terms_info", "syk_term_table", "syk_apply_H",
             "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_expmv_static", "syk_correlator_G",
-            "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read"]
+            "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
+            "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import"]
 
 
 def _check(rc: int, what: str):
@@ -267,3 +271,21 @@ def syk_profile_read(reset: bool = False):
     n, ms = ctypes.c_int64(), ctypes.c_double()
     _check(load().syk_profile_read(ctypes.byref(n), ctypes.byref(ms), int(reset)), "syk_profile_read")
     return {"launches": n.value, "total_ms": ms.value}
+
+
+def syk_autotune_apply(terms: Terms, dtype: int, batch: int, parity: int = 0, reps: int = 2, stream=None) -> float:
+    """Tunes the matvec launch shape for (N, dtype, batch); returns the best ms per apply."""
+    best = ctypes.c_double(0.0)
+    _check(load().syk_autotune_apply(terms.ptr, int(parity), int(dtype), int(batch), int(reps), _stream(stream),
+                                     ctypes.byref(best)), "syk_autotune_apply")
+    return best.value
+
+
+def syk_autotune_export() -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().syk_autotune_export(buf, len(buf)), "syk_autotune_export")
+    return buf.value.decode()
+
+
+def syk_autotune_import(text: str):
+    _check(load().syk_autotune_import(text.encode()), "syk_autotune_import")

@@ -115,3 +115,31 @@ def test_apply_H_invalid_args(torch):
         syk.syk_apply_H(terms, 2, psi)
     with pytest.raises(syk.SykError):
         syk.syk_apply_H(terms, 0, psi[:, :0])
+
+
+@pytest.mark.parametrize("dt,B", [("c64", 8), ("c64", 1), ("c128", 2)])
+def test_apply_H_every_tile_configuration(torch, dt, B):
+    """Every CTA width x cluster size of the tiled matvec (forced through the tuning table)
+    against the oracle, then the autotuner's own choice and its JSON round trip."""
+    N = 24
+    J = inputs.couplings(N, 3)
+    terms = syk.syk_build_terms(N, J)
+    code = syk.SYK_C64 if dt == "c64" else syk.SYK_C128
+    psi = inputs.random_states(N, B, 77)
+    x = to_dev(torch, psi, dt)
+    D = 1 << (N // 2 - 1)
+    rows = np.unique(np.concatenate([[0, D - 1], np.random.default_rng(1).integers(0, D, 40)]))
+    ref = hm.apply_rows(N, J, 0, psi.T, rows)
+    for ntb in (6, 7, 8):
+        for cs in (1, 2, 4, 8):
+            syk.syk_autotune_import('{"apply_tiles": [{"N": %d, "dtype": %d, "batch": %d, "ntb": %d, "cluster": %d}]}'
+                                    % (N, code, B, ntb, cs))
+            y = syk.syk_apply_H(terms, 0, x).cpu().numpy().reshape(D, B)
+            assert rel(y[rows], ref.reshape(len(rows), B)) < TOL[dt], (ntb, cs)
+    best = syk.syk_autotune_apply(terms, code, B)
+    assert best > 0
+    js = syk.syk_autotune_export()
+    assert '"N": 24' in js
+    syk.syk_autotune_import(js)
+    y = syk.syk_apply_H(terms, 0, x).cpu().numpy().reshape(D, B)
+    assert rel(y[rows], ref.reshape(len(rows), B)) < TOL[dt]
