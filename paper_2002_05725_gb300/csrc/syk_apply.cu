@@ -323,8 +323,9 @@ struct TileCfg {
   static size_t smem(int T) { return 2 * buf_bytes(T) + 64; }
 };
 
-// ntb = log2(threads per CTA) in 6..8; a CTA owns T = RPT << ntb rows.
-template <typename R, int BT>
+// ntb = log2(threads per CTA) in 6..8; a CTA owns T = RPT << ntb rows.  CL: launched
+// as clusters that split a tile's mask chunks (otherwise one CTA per tile).
+template <typename R, int BT, bool CL>
 __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* __restrict__ groups, int ngroups,
                                                      int ntb, const typename CT<R>::T* __restrict__ psi,
                                                      typename CT<R>::T* __restrict__ y) {
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   const C* __restrict__ t2 = static_cast<const C*>(p.m2_tab);
   const int tid = threadIdx.x, lane = tid & 31;
   // the CTAs of a cluster share one tile and split its mask chunks round-robin
-  const uint32_t crank = tma::cluster_rank(), csize = tma::cluster_size();
+  const uint32_t crank = CL ? tma::cluster_rank() : 0u, csize = CL ? tma::cluster_size() : 1u;
   const uint32_t tile = blockIdx.x / csize;
   const int nmine = (int)crank < ngroups ? (ngroups - (int)crank + (int)csize - 1) / (int)csize : 0;
   const int n = p.n;
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     __syncthreads();
   }
   // rows are written in the natural layout (logical chunk k of a row at soff[k])
-  unsigned char* dst = csize == 1 ? reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB : sm;
+  unsigned char* dst = !CL ? reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB : sm;
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
     const size_t row = (size_t)(tid + i * NT);
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       for (int k = 0; k < NS; ++k) *reinterpret_cast<S*>(out + soff[k]) = acc[i][k];
     }
   }
-  if (csize > 1) {
+  if constexpr (CL) {
     // every CTA of the cluster reduces 1/csize of the tile's rows over the partial sums
     // held in the cluster's shared memories (fixed rank order: deterministic)
     using V16 = typename Slot<R>::T;
@@ -531,12 +532,14 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   const size_t smem = Cfg::smem(T);
   static size_t attr_set = 0;  // per instantiation: largest dynamic smem enabled so far
   if (smem > attr_set) {
-    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Cfg::smem(Cfg::RPT << 8)));
+    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)Cfg::smem(Cfg::RPT << 8)));
     attr_set = Cfg::smem(Cfg::RPT << 8);
   }
   if (cs == 1) {
-    k_apply_tiled<R, BT><<<(unsigned)ntiles, 1u << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
+    k_apply_tiled<R, BT, false><<<(unsigned)ntiles, 1u << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
                                                                      static_cast<C*>(y));
     count_launch();
     SYK_CUDA_CHECK(cudaGetLastError());
@@ -554,7 +557,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  SYK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_apply_tiled<R, BT>, p, groups, ng, ntb, static_cast<const C*>(psi),
+  SYK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_apply_tiled<R, BT, true>, p, groups, ng, ntb, static_cast<const C*>(psi),
                                     static_cast<C*>(y)));
   count_launch();
   SYK_CUDA_CHECK(cudaGetLastError());
