@@ -246,6 +246,11 @@ def gpu_main(a, rank, world, local_rank):
     psi_dev = psi_host.to(dev).contiguous()
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # untimed: pick the matvec launch shape for this (N, dtype, batch)
+    code = syk.SYK_C64 if a.dtype == "c64" else syk.SYK_C128
+    if a.states in (1, 2, 4, 8, 16):
+        syk.syk_autotune_apply(terms, code, a.states)
+    tuned = json.loads(syk.syk_autotune_export())["apply_tiles"]
 
     def step(src):
         return syk.syk_otoc(terms, a.beta, 0, 1, times, src, krylov_dim=a.krylov, tol=a.tol)
@@ -329,6 +334,7 @@ def gpu_main(a, rank, world, local_rank):
                      "per_launch": {"flops": flops, "avg_ms": avg_ms, "launches": prof["launches"]}},
         "hpsi": {"gather_GBps": gather, "hbm_peak_GBps": pk.get("hbm_gbs"), "gather_frac_of_hbm":
                  gather / float(pk.get("hbm_gbs", 6800.0)), "peak_kind": pk_kind},
+        "apply_tile": next((e for e in tuned if e["N"] == a.N and e["batch"] == a.states), None),
         "applies_per_curve": applies_per_state,
         "applies_per_curve_model": applies_model(a.N, a.beta, times[1:], a.krylov, a.tol),
         "krylov_bases_per_step": cnt["krylov_bases"] / max(1, a.steps),
