@@ -2,7 +2,7 @@
 """Benchmark: regularized-OTOC curves per hour at N = 40 on GB300.
 
 One step = the regularized OTOC F~(t) (Eq. F_reg, rho^{1/4} between the
-operators, W = chi_0, V = chi_1, beta J = 10) of B random states of one
+operators, W = chi_0, V = chi_1, beta J = 10) of B = 16 random states of one
 coupling draw on a 10-point time grid t = 1.2, 2.4, ..., 12 plus t = 0 (the
 10-point curves of Supp. Table I, to the t = 12 of the batched workload),
 Krylov dimension 40, tolerance 1e-7, complex64 vectors with FP64 Lanczos
@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--N", type=int, default=40)
-    ap.add_argument("--states", type=int, default=8)
+    ap.add_argument("--states", type=int, default=16)
     ap.add_argument("--beta", type=float, default=10.0)
     ap.add_argument("--npts", type=int, default=10)
     ap.add_argument("--tmax", type=float, default=12.0)
@@ -65,6 +65,27 @@ def peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def ncu_traffic(N, states, dtype):
+    """DRAM bytes per matvec launch from the committed ncu summary of this configuration,
+    or None if there is none or the kernel source changed since it was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"apply_tiled_N{N}_B{states}_{dtype}.md")
+    src = os.path.join(ROOT, "paper_2002_05725_gb300", "csrc", "syk_apply.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None, None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != sha or "traffic_bytes_per_launch" not in vals:
+        return None, os.path.relpath(path, ROOT)
+    return float(vals["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -320,6 +341,7 @@ def gpu_main(a, rank, world, local_rank):
     if a.dtype == "c128":
         peak = peak / 64.0  # FP64 FMA rate of GB300 is 1/64 of FP32
     achieved = flops / (avg_ms * 1e-3) / 1e12
+    traffic, traffic_src = ncu_traffic(a.N, a.states, a.dtype)
     esz = 8 if a.dtype == "c64" else 16
     gather = nnz * a.states * esz / (avg_ms * 1e-3) / 1e9
     line = {
@@ -328,7 +350,7 @@ def gpu_main(a, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
         "config": config_dict(a, times),
         "roofline": {"kernel": "apply_H (k_apply_tiled)", "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
                                   + (" / 64 (FP64)" if a.dtype == "c128" else ""),
                      "per_launch": {"flops": flops, "avg_ms": avg_ms, "launches": prof["launches"]}},
