@@ -168,6 +168,30 @@ int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t,
              const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
              double* F_re_im, void* stream);
 
+/* --------------------------------------------------------------- gradients
+ * syk_otoc_grad -- F~(t) = F(t)/F(0) of syk_otoc at one time t for each state,
+ * with its derivatives with respect to every coupling J_ijkl (Eq. 1) and beta.
+ * The correlators are sesquilinear forms of chains of exponentials e^{zH} and
+ * Majoranas; each exponential is differentiated with Duhamel's formula
+ *   d e^{zH}/dJ_T = z int_0^1 e^{(1-v)zH} P_T e^{vzH} dv,  P_T = chi_i chi_j chi_k chi_l,
+ * integrated with 4-point Gauss-Legendre on sub-intervals of |z| rho <= quad_dz
+ * (rho = 3 sqrt(sum J^2/16), a scale of the spectral radius), with the forward
+ * states checkpointed every ceil(sqrt(#sub-intervals)) and recomputed per segment;
+ * <lam|P_T|psi> for all terms is one pass over the state per quadrature node.
+ * d e^{-c beta H}/dbeta = -c H e^{-c beta H}.  The paper computes no gradients;
+ * the correlators differentiated are its Eq. F_reg and Eq. G.
+ * psi0: D x nstates, device or host memory (even sector).  Host outputs:
+ * Ft_re_im[2*s..], dFt_dJ[(T*nstates + s)*2 + {0,1}] (C(N,4) x nstates complex),
+ * dFt_dbeta[2*s..].  Synchronises `stream`. */
+int syk_otoc_grad(const syk_terms* terms, double beta, int i, int j, double t, const void* psi0,
+                  int64_t nstates, int dtype, int krylov_dim, double tol, double quad_dz,
+                  double* Ft_re_im, double* dFt_dJ, double* dFt_dbeta, void* stream);
+/* syk_correlator_G_grad -- G(t) of syk_correlator_G at one time t (normalised by
+ * Z = <phi|phi>) per state, with dG/dJ_T and dG/dbeta; conventions as syk_otoc_grad. */
+int syk_correlator_G_grad(const syk_terms* terms, double beta, int i, double t, const void* psi0,
+                          int64_t nstates, int dtype, int krylov_dim, double tol, double quad_dz,
+                          double* G_re_im, double* dG_dJ, double* dG_dbeta, void* stream);
+
 /* ------------------------------------------------------------- autotuner
  * syk_autotune_apply -- times every tile configuration of the tiled matvec
  * (CTA width 64/128/256 threads x thread-block cluster of 1/2/4/8 CTAs sharing a

@@ -1,0 +1,586 @@
+// Gradients of the correlators with respect to every coupling J_ijkl and beta
+// (reverse mode through the Krylov evolutions).
+//
+// A correlator is a sesquilinear form <a|b> of two chains of operators applied to
+// the random states: a = A_K..A_1 psi~, b = B_L..B_1 psi~, each operator either an
+// exponential e^{zH} (z = -c_beta beta - i c_t t) or one Majorana chi_i (Eq. F_reg,
+// Eq. G, Eq. q_typicality).  For an exponential M = e^{zH} with input x and the
+// adjoint vector lam at its output, Duhamel's formula gives
+//   <lam| dM/dJ_T |x> = z int_0^1 <e^{(1-v) conj(z) H} lam| P_T |e^{v z H} x> dv,
+// P_T = dH/dJ_T = chi_i chi_j chi_k chi_l (Eq. 1).  The integral is split into S
+// sub-intervals with 4 Gauss-Legendre nodes each.  The adjoint lam(v) marches from
+// v = 1 down to 0 while the forward state psi(v) is needed in the same decreasing
+// order, so psi is checkpointed every ceil(sqrt(S)) sub-intervals on a forward
+// sweep and each segment is recomputed from its checkpoint (O(sqrt S) stored states).
+// At every node one pass over the state (K6, k_term_grad) accumulates
+// <lam|P_T|psi> for all C(N,4) terms at once: terms sharing an X-mask and the
+// Z-mask bits off their support form one group, and each row adds
+// conj(lam[x]) psi[x^m] (-1)^popcount(zeta & x) with the signs (-1)^popcount(s & u(x))
+// of the group's 2^k terms.  d/dbeta of e^{-c beta H} is -c H e^{-c beta H}.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "syk_cplx.cuh"
+#include "syk_krylov.cuh"
+
+namespace syk {
+namespace {
+
+__device__ __forceinline__ uint32_t grad_supp_bits(uint32_t xf, uint32_t s) {
+  return (__funnelshift_r(xf, 0u, s) & 1u) | (__funnelshift_r(xf, 0u, s >> 8) & 2u) |
+         (__funnelshift_r(xf, 0u, s >> 16) & 4u) | (__funnelshift_r(xf, 0u, s >> 24) & 8u);
+}
+
+// partial[((g*RC + chunk)*16 + s)*B + b] = sum over the chunk's rows of
+// conj(lam[x][b]) psi[x^m][b] (-1)^popcount(zeta & xf) (-1)^popcount(s & u(xf))
+template <typename R>
+__global__ void k_term_grad(const uint4* __restrict__ grec, int n, int sector, int64_t D, int B,
+                            const typename CT<R>::T* __restrict__ lam, const typename CT<R>::T* __restrict__ psi,
+                            double2* __restrict__ partial) {
+  using C = typename CT<R>::T;
+  extern __shared__ double2 red[];
+  const int g = blockIdx.x, chunk = blockIdx.y, RC = gridDim.y;
+  const uint4 rec = __ldg(&grec[g]);
+  const int k = (int)rec.w;
+  const int ns = 1 << k;
+  const int b = threadIdx.x % B;
+  const int rows_per_pass = blockDim.x / B;
+  const int64_t per = (D + RC - 1) / RC;
+  const int64_t r0 = (int64_t)chunk * per, r1 = min(D, r0 + per);
+  R ar[16], ai[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) ar[s] = ai[s] = R(0);
+  for (int64_t x = r0 + threadIdx.x / B; x < r1; x += rows_per_pass) {
+    const uint32_t xc = (uint32_t)x;
+    const uint32_t xf = xc | ((uint32_t)((__popc(xc) + sector) & 1) << (n - 1));
+    const C l = lam[x * B + b];
+    const C p = psi[(int64_t)(xc ^ rec.x) * B + b];
+    R cr = l.x * p.x + l.y * p.y;  // conj(l) * p
+    R ci = l.x * p.y - l.y * p.x;
+    if (__popc(rec.y & xf) & 1) {
+      cr = -cr;
+      ci = -ci;
+    }
+    const uint32_t u = grad_supp_bits(xf, rec.z) & (uint32_t)(ns - 1);
+#pragma unroll
+    for (int s = 0; s < 16; ++s)
+      if (s < ns) {
+        const bool neg = __popc((uint32_t)s & u) & 1;
+        ar[s] += neg ? -cr : cr;
+        ai[s] += neg ? -ci : ci;
+      }
+  }
+  for (int s = 0; s < ns; ++s) {
+    red[threadIdx.x] = make_double2((double)ar[s], (double)ai[s]);
+    __syncthreads();
+    if ((int)threadIdx.x < B) {
+      double sx = 0.0, sy = 0.0;
+      for (int t = threadIdx.x; t < (int)blockDim.x; t += B) {
+        sx += red[t].x;
+        sy += red[t].y;
+      }
+      partial[(((size_t)g * RC + chunk) * 16 + s) * B + threadIdx.x] = make_double2(sx, sy);
+    }
+    __syncthreads();
+  }
+}
+
+// acc[T*B + b] += coef * phase_T * sum_chunks partial[group(T), chunk, s(T), b]
+__global__ void k_term_grad_accum(int64_t nterms, int B, int RC, const int* __restrict__ tgroup,
+                                  const uint8_t* __restrict__ ts, const double2* __restrict__ tphase,
+                                  const double2* __restrict__ partial, double cre, double cim,
+                                  double2* __restrict__ acc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nterms * B) return;
+  const int64_t T = idx / B;
+  const int b = (int)(idx - T * B);
+  const int g = tgroup[T], s = ts[T];
+  double vx = 0.0, vy = 0.0;
+  for (int c = 0; c < RC; ++c) {
+    const double2 p = partial[(((size_t)g * RC + c) * 16 + s) * B + b];
+    vx += p.x;
+    vy += p.y;
+  }
+  const double2 ph = tphase[T];
+  const double wx = ph.x * vx - ph.y * vy, wy = ph.x * vy + ph.y * vx;  // phase * v
+  double2 a = acc[idx];
+  a.x += cre * wx - cim * wy;
+  a.y += cre * wy + cim * wx;
+  acc[idx] = a;
+}
+
+// out[T*B + b] += coef[b] * (gb[T*B + b] + conj(ga[T*B + b]))   (T < nrows)
+__global__ void k_grad_combine(int64_t nrows, int B, const double2* __restrict__ gb, const double2* __restrict__ ga,
+                               const double2* __restrict__ coef, double2* __restrict__ out) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nrows * B) return;
+  const int b = (int)(idx % B);
+  const double vx = gb[idx].x + ga[idx].x, vy = gb[idx].y - ga[idx].y;
+  const double2 c = coef[b];
+  double2 o = out[idx];
+  o.x += c.x * vx - c.y * vy;
+  o.y += c.x * vy + c.y * vx;
+  out[idx] = o;
+}
+
+// acc[b] += coef * d[b]
+__global__ void k_axpy_cols(int B, const double2* __restrict__ d, double cre, double cim, double2* __restrict__ acc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double2 v = d[b];
+  acc[b].x += cre * v.x - cim * v.y;
+  acc[b].y += cre * v.y + cim * v.x;
+}
+
+struct Op {
+  int kind;   // 0: e^{zH}, z = -cb*beta - i*ct*t;  1: chi_maj
+  double cb, ct;
+  int maj;
+};
+
+// Gauss-Legendre nodes and weights on [-1, 1] (4 points)
+const double kGLx[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
+const double kGLw[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
+
+struct GradEngine {
+  const syk_terms* terms = nullptr;
+  int dtype = 0, krylov = 0;
+  int64_t B = 0, D = 0;
+  double beta = 0, t = 0, tol = 0, rho = 1.0, dz = 0.05;  // dz: max |z| per sub-interval
+  cudaStream_t st = nullptr;
+  ApplyParams P[2];
+  KrylovWS ws;
+  std::vector<void*> owned;
+  size_t vb = 0;
+  int RC = 1, bdim = 0;
+  double2* partial = nullptr;
+  double2* dots = nullptr;  // B
+
+  ~GradEngine() {
+    for (void* p : owned) cudaFreeAsync(p, st);
+  }
+  int alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+      set_error("gradient: cannot allocate %zu bytes: %s", bytes, cudaGetErrorString(e));
+      *p = nullptr;
+      return SYK_ENOMEM;
+    }
+    owned.push_back(*p);
+    return SYK_OK;
+  }
+  int vec(void** p) { return alloc(p, vb); }
+  // reusable state vectors (returned with put)
+  std::vector<void*> free_vecs;
+  int get(void** p) {
+    if (!free_vecs.empty()) {
+      *p = free_vecs.back();
+      free_vecs.pop_back();
+      return SYK_OK;
+    }
+    return vec(p);
+  }
+  void put(void* p) {
+    if (p) free_vecs.push_back(p);
+  }
+
+  int init() {
+    SYK_TRY(make_apply_params(terms, 0, dtype, &P[0]));
+    SYK_TRY(make_apply_params(terms, 1, dtype, &P[1]));
+    SYK_TRY(ensure_grad_groups(terms));
+    D = terms->D;
+    vb = size_t(D) * B * dtype_size(dtype);
+    void* w = nullptr;
+    const size_t wsb = krylov_ws_bytes(D, dtype, krylov, B);
+    SYK_TRY(alloc(&w, wsb));
+    SYK_TRY(krylov_ws_carve(&ws, w, wsb, D, dtype, krylov, B));
+    bdim = int(B) * std::max(1, int(256 / B));
+    const int64_t rows_per_pass = bdim / B;
+    RC = int(std::max<int64_t>(1, std::min<int64_t>(64, D / (rows_per_pass * 16))));
+    void* p = nullptr;
+    SYK_TRY(alloc(&p, sizeof(double2) * size_t(terms->ngg) * RC * 16 * B));
+    partial = static_cast<double2*>(p);
+    SYK_TRY(alloc(&p, sizeof(double2) * B));
+    dots = static_cast<double2*>(p);
+    // spectral-radius scale of H for the quadrature step: 3 x sqrt(Tr H^2 / dim) = 3 sqrt(sum J^2 / 16)
+    double s2 = 0.0;
+    for (double j : terms->J) s2 += j * j;
+    rho = 3.0 * std::sqrt(s2 / 16.0);
+    return SYK_OK;
+  }
+
+  std::complex<double> z_of(const Op& o) const { return {-o.cb * beta, -o.ct * t}; }
+
+  int expmv(int sector, std::complex<double> z, const void* in, void* out) {
+    return expmv_impl(P[sector], dtype, z, in, out, B, tol, ws, st, nullptr);
+  }
+  int copy(void* dst, const void* src) {
+    SYK_CUDA_CHECK(cudaMemcpyAsync(dst, src, vb, cudaMemcpyDeviceToDevice, st));
+    return SYK_OK;
+  }
+
+  // acc[T][b] += coef * <lam|P_T|psi>
+  int term_grad(int sector, const void* lam, const void* psi, std::complex<double> coef, double2* acc) {
+    dim3 grid(terms->ngg, RC);
+    if (dtype == SYK_C64)
+      k_term_grad<float><<<grid, bdim, bdim * sizeof(double2), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
+                                                                     (const float2*)lam, (const float2*)psi, partial);
+    else
+      k_term_grad<double><<<grid, bdim, bdim * sizeof(double2), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
+                                                                      (const double2*)lam, (const double2*)psi, partial);
+    const int64_t n = terms->nterms * B;
+    k_term_grad_accum<<<unsigned((n + 255) / 256), 256, 0, st>>>(terms->nterms, int(B), RC, terms->d_term_group,
+                                                                 terms->d_term_s, terms->d_term_phase, partial,
+                                                                 coef.real(), coef.imag(), acc);
+    count_launch(2);
+    SYK_CUDA_CHECK(cudaGetLastError());
+    return SYK_OK;
+  }
+
+  // Forward pass of a chain: xs[k] = input of op k (xs[0] = psi), returns output sectors.
+  int forward(const std::vector<Op>& ops, const void* psi, std::vector<void*>& xs, std::vector<int>& sec) {
+    xs.assign(ops.size() + 1, nullptr);
+    sec.assign(ops.size() + 1, 0);
+    xs[0] = const_cast<void*>(psi);
+    for (size_t k = 0; k < ops.size(); ++k) {
+      SYK_TRY(get(&xs[k + 1]));
+      const Op& o = ops[k];
+      if (o.kind == 1) {
+        SYK_TRY(launch_apply_chi(terms->N, o.maj, sec[k], dtype, xs[k], xs[k + 1], B, st));
+        sec[k + 1] = 1 - sec[k];
+      } else {
+        SYK_TRY(expmv(sec[k], z_of(o), xs[k], xs[k + 1]));
+        sec[k + 1] = sec[k];
+      }
+    }
+    return SYK_OK;
+  }
+
+  // lam: adjoint at the output of the exponential (overwritten with the adjoint at its input);
+  // x: input; y: output.  Adds <lam|dM/dJ_T|x> to gJ and <lam|dM/dbeta|x> to gb.
+  int exp_adjoint(const Op& o, int sector, const void* x, const void* y, void* lam, double2* gJ, double2* gb) {
+    const std::complex<double> z = z_of(o);
+    if (z == std::complex<double>(0.0, 0.0)) return SYK_OK;  // identity
+    if (o.cb != 0.0) {
+      // d/dbeta e^{-cb beta H} = -cb H e^{-cb beta H}:  <lam| -cb H y>
+      void* hy = nullptr;
+      SYK_TRY(get(&hy));
+      SYK_TRY(launch_apply_H(P[sector], dtype, y, hy, B, st));
+      SYK_TRY(dot_columns(lam, hy, D, B, dtype, ws, dots, st));
+      k_axpy_cols<<<unsigned((B + 127) / 128), 128, 0, st>>>(int(B), dots, -o.cb, 0.0, gb);
+      count_launch();
+      put(hy);
+    }
+    const int S = std::max(1, int(std::ceil(std::abs(z) * rho / dz)));
+    const int c = std::max(1, int(std::ceil(std::sqrt(double(S)))));
+    const int nseg = (S + c - 1) / c;
+    const std::complex<double> zs = z / double(S), zbar = std::conj(z);
+    std::vector<void*> ckpt(nseg), segbuf(c), node(4);
+    for (auto& p : ckpt) SYK_TRY(get(&p));
+    for (auto& p : segbuf) SYK_TRY(get(&p));
+    for (auto& p : node) SYK_TRY(get(&p));
+    // forward sweep: checkpoints psi(s/S) for s = 0, c, 2c, ...
+    SYK_TRY(copy(ckpt[0], x));
+    for (int sg = 1; sg < nseg; ++sg) {
+      SYK_TRY(copy(ckpt[sg], ckpt[sg - 1]));
+      for (int s = 0; s < c; ++s) SYK_TRY(expmv(sector, zs, ckpt[sg], ckpt[sg]));
+    }
+    // backward: lam(v) marches from v = 1 to 0
+    double vcur = 1.0;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int s0 = sg * c, s1 = std::min(S, s0 + c);
+      SYK_TRY(copy(segbuf[0], ckpt[sg]));
+      for (int s = s0 + 1; s < s1; ++s) SYK_TRY(expmv(sector, zs, segbuf[s - s0 - 1], segbuf[s - s0]));
+      for (int s = s1 - 1; s >= s0; --s) {
+        // forward states at the 4 nodes of [s/S, (s+1)/S], ascending
+        double vq[4];
+        for (int q = 0; q < 4; ++q) vq[q] = (s + 0.5 * (1.0 + kGLx[q])) / S;
+        double vprev = double(s) / S;
+        const void* from = segbuf[s - s0];
+        for (int q = 0; q < 4; ++q) {
+          SYK_TRY(expmv(sector, z * (vq[q] - vprev), from, node[q]));
+          from = node[q];
+          vprev = vq[q];
+        }
+        for (int q = 3; q >= 0; --q) {
+          SYK_TRY(expmv(sector, zbar * (vcur - vq[q]), lam, lam));
+          vcur = vq[q];
+          SYK_TRY(term_grad(sector, lam, node[q], z * (0.5 * kGLw[q] / S), gJ));
+        }
+        SYK_TRY(expmv(sector, zbar * (vcur - double(s) / S), lam, lam));
+        vcur = double(s) / S;
+      }
+    }
+    for (auto p : ckpt) put(p);
+    for (auto p : segbuf) put(p);
+    for (auto p : node) put(p);
+    return SYK_OK;
+  }
+
+  // Raw gradient of <left| chain psi>: gJ[T][b] += <left|d chain/dJ_T|psi>, gb[b] likewise.
+  int chain_grad(const std::vector<Op>& ops, const void* psi, const void* left, double2* gJ, double2* gb) {
+    std::vector<void*> xs;
+    std::vector<int> sec;
+    SYK_TRY(forward(ops, psi, xs, sec));
+    void* lam = nullptr;
+    SYK_TRY(get(&lam));
+    SYK_TRY(copy(lam, left));
+    for (int k = int(ops.size()) - 1; k >= 0; --k) {
+      const Op& o = ops[k];
+      if (o.kind == 1) {
+        void* tmp = nullptr;
+        SYK_TRY(get(&tmp));
+        SYK_TRY(launch_apply_chi(terms->N, o.maj, sec[k + 1], dtype, lam, tmp, B, st));
+        put(lam);
+        lam = tmp;
+      } else {
+        SYK_TRY(exp_adjoint(o, sec[k], xs[k], xs[k + 1], lam, gJ, gb));
+      }
+    }
+    put(lam);
+    for (size_t k = 1; k < xs.size(); ++k) put(xs[k]);
+    return SYK_OK;
+  }
+
+  // Value <a|b> (device, B entries) of two chains.
+  int value(const std::vector<Op>& A, const std::vector<Op>& Bc, const void* psi, double2* out, void** a_out,
+            void** b_out) {
+    std::vector<void*> xa, xb;
+    std::vector<int> sa, sb;
+    SYK_TRY(forward(A, psi, xa, sa));
+    SYK_TRY(forward(Bc, psi, xb, sb));
+    SYK_TRY(dot_columns(xa.back(), xb.back(), D, B, dtype, ws, out, st));
+    *a_out = xa.back();
+    *b_out = xb.back();
+    return SYK_OK;
+  }
+
+  // out_J[T][b] += coef[b] * d<a|b>/dJ_T, out_b[b] += coef[b] * d<a|b>/dbeta
+  int form_grad(const std::vector<Op>& A, const std::vector<Op>& Bc, const void* psi, const void* a, const void* b,
+                const double2* coef, double2* out_J, double2* out_b) {
+    const size_t nJ = sizeof(double2) * size_t(terms->nterms) * B;
+    void *gJa, *gJb, *gba, *gbb;
+    SYK_TRY(alloc(&gJa, nJ));
+    SYK_TRY(alloc(&gJb, nJ));
+    SYK_TRY(alloc(&gba, sizeof(double2) * B));
+    SYK_TRY(alloc(&gbb, sizeof(double2) * B));
+    cudaMemsetAsync(gJa, 0, nJ, st);
+    cudaMemsetAsync(gJb, 0, nJ, st);
+    cudaMemsetAsync(gba, 0, sizeof(double2) * B, st);
+    cudaMemsetAsync(gbb, 0, sizeof(double2) * B, st);
+    SYK_TRY(chain_grad(Bc, psi, a, (double2*)gJb, (double2*)gbb));  // <a|db>
+    SYK_TRY(chain_grad(A, psi, b, (double2*)gJa, (double2*)gba));   // <b|da> = conj(<da|b>)
+    const int64_t n = terms->nterms * B;
+    k_grad_combine<<<unsigned((n + 255) / 256), 256, 0, st>>>(terms->nterms, int(B), (double2*)gJb, (double2*)gJa,
+                                                              coef, out_J);
+    k_grad_combine<<<1, 256, 0, st>>>(1, int(B), (double2*)gbb, (double2*)gba, coef, out_b);
+    count_launch(2);
+    SYK_CUDA_CHECK(cudaGetLastError());
+    return SYK_OK;
+  }
+};
+
+std::vector<Op> otoc_A(int i) {
+  return {{0, 1.0 / 8, 0, 0}, {0, 0, 1.0, 0}, {1, 0, 0, i}, {0, 0, -1.0, 0}, {0, 1.0 / 4, 0, 0}};
+}
+std::vector<Op> otoc_B(int i, int j) {
+  return {{0, 1.0 / 8, 0, 0}, {1, 0, 0, j}, {0, 1.0 / 4, 0, 0}, {0, 0, 1.0, 0},
+          {1, 0, 0, i},       {0, 0, -1.0, 0}, {0, 1.0 / 4, 0, 0}, {1, 0, 0, j}};
+}
+
+int grad_common_checks(const syk_terms* terms, double beta, double t, const void* psi0, int64_t ns, int dtype, int kd,
+                       double tol, double dz) {
+  if (!terms || !psi0) {
+    set_error("NULL argument");
+    return SYK_EINVAL;
+  }
+  if (!std::isfinite(beta) || beta < 0.0 || !std::isfinite(t) || t < 0.0) {
+    set_error("beta and t must be finite and >= 0");
+    return SYK_EINVAL;
+  }
+  if (ns < 1 || ns > 256 || kd < 2 || kd > SYK_MAX_KRYLOV || !dtype_ok(dtype) || !(tol > 0.0) || !(dz > 0.0)) {
+    set_error("invalid sizes (nstates=%lld krylov_dim=%d dtype=%d tol=%g quad_dz=%g)", (long long)ns, kd, dtype, tol,
+              dz);
+    return SYK_EINVAL;
+  }
+  return SYK_OK;
+}
+
+int device_input_copy(GradEngine& E, const void* psi0, const void** out) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, psi0);
+  if (e != cudaSuccess) cudaGetLastError();
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+    *out = psi0;
+    return SYK_OK;
+  }
+  void* d = nullptr;
+  SYK_TRY(E.vec(&d));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(d, psi0, E.vb, cudaMemcpyHostToDevice, E.st));
+  *out = d;
+  return SYK_OK;
+}
+
+int finish_outputs(GradEngine& E, const double2* val, const double2* gJ, const double2* gb, double* v_re_im,
+                   double* dJ, double* db) {
+  const size_t B = size_t(E.B), nt = size_t(E.terms->nterms);
+  std::vector<double2> hv(B), hb(B);
+  SYK_CUDA_CHECK(cudaMemcpyAsync(hv.data(), val, sizeof(double2) * B, cudaMemcpyDeviceToHost, E.st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(hb.data(), gb, sizeof(double2) * B, cudaMemcpyDeviceToHost, E.st));
+  if (dJ) SYK_CUDA_CHECK(cudaMemcpyAsync(dJ, gJ, sizeof(double2) * nt * B, cudaMemcpyDeviceToHost, E.st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(E.st));
+  prof_collect();
+  for (size_t b = 0; b < B; ++b) {
+    if (v_re_im) {
+      v_re_im[2 * b] = hv[b].x;
+      v_re_im[2 * b + 1] = hv[b].y;
+    }
+    if (db) {
+      db[2 * b] = hb[b].x;
+      db[2 * b + 1] = hb[b].y;
+    }
+  }
+  return SYK_OK;
+}
+
+}  // namespace
+}  // namespace syk
+
+using namespace syk;
+
+extern "C" int syk_otoc_grad(const syk_terms* terms, double beta, int i, int j, double t, const void* psi0,
+                             int64_t nstates, int dtype, int krylov_dim, double tol, double quad_dz,
+                             double* Ft_re_im, double* dFt_dJ, double* dFt_dbeta, void* stream) {
+  clear_error();
+  SYK_TRY(grad_common_checks(terms, beta, t, psi0, nstates, dtype, krylov_dim, tol, quad_dz));
+  if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
+    set_error("syk_otoc_grad: need 0 <= i != j < N");
+    return SYK_EINVAL;
+  }
+  GradEngine E;
+  E.terms = terms;
+  E.dtype = dtype;
+  E.krylov = krylov_dim;
+  E.B = nstates;
+  E.beta = beta;
+  E.tol = tol;
+  E.dz = quad_dz;
+  E.st = static_cast<cudaStream_t>(stream);
+  SYK_TRY(E.init());
+  const void* psi = nullptr;
+  SYK_TRY(device_input_copy(E, psi0, &psi));
+  const std::vector<Op> A = otoc_A(i), Bc = otoc_B(i, j);
+  const size_t B = size_t(nstates);
+  // values F(t) and F(0)
+  void *vt, *v0, *a_t, *b_t, *a_0, *b_0;
+  SYK_TRY(E.alloc(&vt, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&v0, sizeof(double2) * B));
+  E.t = t;
+  SYK_TRY(E.value(A, Bc, psi, (double2*)vt, &a_t, &b_t));
+  E.t = 0.0;
+  SYK_TRY(E.value(A, Bc, psi, (double2*)v0, &a_0, &b_0));
+  std::vector<double2> ht(B), h0(B);
+  SYK_CUDA_CHECK(cudaMemcpyAsync(ht.data(), vt, sizeof(double2) * B, cudaMemcpyDeviceToHost, E.st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(h0.data(), v0, sizeof(double2) * B, cudaMemcpyDeviceToHost, E.st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(E.st));
+  // F~ = F_t / F_0;  dF~ = dF_t / F_0 - F~ dF_0 / F_0
+  std::vector<double2> ctv(B), c0v(B), ft(B);
+  for (size_t b = 0; b < B; ++b) {
+    const std::complex<double> Ft(ht[b].x, ht[b].y), F0(h0[b].x, h0[b].y);
+    if (std::abs(F0) == 0.0) {
+      set_error("syk_otoc_grad: F(0) = 0 for state %zu", b);
+      return SYK_ENUMERIC;
+    }
+    const std::complex<double> Ftil = Ft / F0, c1 = 1.0 / F0, c0 = -Ftil / F0;
+    ft[b] = make_double2(Ftil.real(), Ftil.imag());
+    ctv[b] = make_double2(c1.real(), c1.imag());
+    c0v[b] = make_double2(c0.real(), c0.imag());
+  }
+  void *ct, *c0, *gJ, *gb, *ftd;
+  const size_t nJ = sizeof(double2) * size_t(terms->nterms) * B;
+  SYK_TRY(E.alloc(&ct, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&c0, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&ftd, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&gJ, nJ));
+  SYK_TRY(E.alloc(&gb, sizeof(double2) * B));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(ct, ctv.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, E.st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(c0, c0v.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, E.st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(ftd, ft.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, E.st));
+  cudaMemsetAsync(gJ, 0, nJ, E.st);
+  cudaMemsetAsync(gb, 0, sizeof(double2) * B, E.st);
+  E.t = t;
+  SYK_TRY(E.form_grad(A, Bc, psi, a_t, b_t, (double2*)ct, (double2*)gJ, (double2*)gb));
+  E.t = 0.0;
+  SYK_TRY(E.form_grad(A, Bc, psi, a_0, b_0, (double2*)c0, (double2*)gJ, (double2*)gb));
+  return finish_outputs(E, (double2*)ftd, (double2*)gJ, (double2*)gb, Ft_re_im, dFt_dJ, dFt_dbeta);
+}
+
+extern "C" int syk_correlator_G_grad(const syk_terms* terms, double beta, int i, double t, const void* psi0,
+                                     int64_t nstates, int dtype, int krylov_dim, double tol, double quad_dz,
+                                     double* G_re_im, double* dG_dJ, double* dG_dbeta, void* stream) {
+  clear_error();
+  SYK_TRY(grad_common_checks(terms, beta, t, psi0, nstates, dtype, krylov_dim, tol, quad_dz));
+  if (i < 0 || i >= terms->N) {
+    set_error("syk_correlator_G_grad: Majorana index out of range");
+    return SYK_EINVAL;
+  }
+  GradEngine E;
+  E.terms = terms;
+  E.dtype = dtype;
+  E.krylov = krylov_dim;
+  E.B = nstates;
+  E.beta = beta;
+  E.t = t;
+  E.tol = tol;
+  E.dz = quad_dz;
+  E.st = static_cast<cudaStream_t>(stream);
+  SYK_TRY(E.init());
+  const void* psi = nullptr;
+  SYK_TRY(device_input_copy(E, psi0, &psi));
+  const std::vector<Op> A = {{0, 0.5, 0, 0}, {0, 0, 1.0, 0}};
+  const std::vector<Op> Bc = {{0, 0.5, 0, 0}, {1, 0, 0, i}, {0, 0, 1.0, 0}, {1, 0, 0, i}};
+  const std::vector<Op> Zc = {{0, 0.5, 0, 0}};
+  const size_t B = size_t(nstates);
+  void *vn, *vz, *a, *b, *za, *zb;
+  SYK_TRY(E.alloc(&vn, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&vz, sizeof(double2) * B));
+  SYK_TRY(E.value(A, Bc, psi, (double2*)vn, &a, &b));
+  SYK_TRY(E.value(Zc, Zc, psi, (double2*)vz, &za, &zb));
+  std::vector<double2> hn(B), hz(B);
+  SYK_CUDA_CHECK(cudaMemcpyAsync(hn.data(), vn, sizeof(double2) * B, cudaMemcpyDeviceToHost, E.st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(hz.data(), vz, sizeof(double2) * B, cudaMemcpyDeviceToHost, E.st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(E.st));
+  // G = num / Z;  dG = dnum / Z - G dZ / Z
+  std::vector<double2> cn(B), cz(B), gv(B);
+  for (size_t k = 0; k < B; ++k) {
+    const std::complex<double> num(hn[k].x, hn[k].y);
+    const double Z = hz[k].x;
+    if (!(Z > 0.0)) {
+      set_error("syk_correlator_G_grad: Z <= 0 for state %zu", k);
+      return SYK_ENUMERIC;
+    }
+    const std::complex<double> G = num / Z, c1 = 1.0 / Z, c0 = -G / Z;
+    gv[k] = make_double2(G.real(), G.imag());
+    cn[k] = make_double2(c1.real(), c1.imag());
+    cz[k] = make_double2(c0.real(), c0.imag());
+  }
+  void *dcn, *dcz, *gJ, *gb, *gvd;
+  const size_t nJ = sizeof(double2) * size_t(terms->nterms) * B;
+  SYK_TRY(E.alloc(&dcn, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&dcz, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&gvd, sizeof(double2) * B));
+  SYK_TRY(E.alloc(&gJ, nJ));
+  SYK_TRY(E.alloc(&gb, sizeof(double2) * B));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(dcn, cn.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, E.st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(dcz, cz.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, E.st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(gvd, gv.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, E.st));
+  cudaMemsetAsync(gJ, 0, nJ, E.st);
+  cudaMemsetAsync(gb, 0, sizeof(double2) * B, E.st);
+  SYK_TRY(E.form_grad(A, Bc, psi, a, b, (double2*)dcn, (double2*)gJ, (double2*)gb));
+  SYK_TRY(E.form_grad(Zc, Zc, psi, za, zb, (double2*)dcz, (double2*)gJ, (double2*)gb));
+  return finish_outputs(E, (double2*)gvd, (double2*)gJ, (double2*)gb, G_re_im, dG_dJ, dG_dbeta);
+}

@@ -70,6 +70,7 @@ int tile_groups(const syk_terms* t, int tb, int gmax, const int4** dev, int* cou
 bool tile_groups_cached(const syk_terms* t, int tb, int gmax, const int4** dev, int* count);
 
 int ensure_device_tables(const syk_terms* t);
+int ensure_grad_groups(const syk_terms* t);  // builds and uploads the gradient term groups
 int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p);
 
 // Kernel launchers (stream-ordered, no synchronisation).
@@ -105,5 +106,16 @@ struct syk_terms {
   std::vector<double> wdiag;     // n * n
   mutable syk::DeviceTables dev;
   mutable std::map<int, std::pair<int4*, int>> groups_dev;  // tile bits -> device group list
+  // Term groups of the per-term inner products (gradients), built on first use: terms sharing
+  // an X-mask and a Z-mask off their support bits; device copies on dev.device.
+  mutable int ngg = 0;
+  mutable std::vector<uint32_t> gg_rec;   // 4 words per group: compact xor, zeta, support shifts, k
+  mutable std::vector<int32_t> term_group;
+  mutable std::vector<uint8_t> term_s;
+  mutable std::vector<double> term_phase;  // 2 per term: i^p (-1)^popcount(z & m) / 4
+  mutable uint4* d_gg_rec = nullptr;
+  mutable int* d_term_group = nullptr;
+  mutable uint8_t* d_term_s = nullptr;
+  mutable double2* d_term_phase = nullptr;
   mutable std::mutex mtx;
 };

@@ -546,7 +546,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
       count_launch();
       if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
       const bool last = (j + 1 == m);
-      if (last || ((j + 1) % 8 == 0)) {
+      if (last || j + 1 == 4 || ((j + 1) % 8 == 0)) {
         const int mm = j + 1;
         const size_t smem = sizeof(double) * (size_t(mm) * mm + 2 * mm + 2);
         k_tridiag_eig<<<int(B), 32, smem, st>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem,

@@ -90,6 +90,7 @@ std::complex<double> ipow(int p) {
 }
 
 }  // namespace
+
 }  // namespace syk
 
 using syk::set_error;
@@ -279,6 +280,9 @@ extern "C" void syk_free_terms(syk_terms* t) {
       if (p) cudaFree(p);
     for (auto& kv : t->groups_dev)
       if (kv.second.first) cudaFree(kv.second.first);
+    void* gp[] = {t->d_gg_rec, t->d_term_group, t->d_term_s, t->d_term_phase};
+    for (void* p : gp)
+      if (p) cudaFree(p);
     if (prev >= 0) cudaSetDevice(prev);
   }
   delete t;
@@ -424,5 +428,80 @@ int tile_groups(const syk_terms* t, int tb, int gmax, const int4** out, int* cou
   *count = it->second.second;
   return SYK_OK;
 }
+
+
+// Gradient term groups.  For term T with X-mask m and Z-mask z_T the matrix element is
+// (P_T psi)[x] = (i^p/4) (-1)^popcount(z_T & (x^m)) psi[x^m].  Terms are grouped so that
+// z_T = zeta ^ spread(s_T) with s_T the bits of z_T at k "support" positions:
+//   popcount-4 masks: the 4 spins of m (k = 4, 16 terms);
+//   popcount-2 masks: one group per (m, doubled spin c), zeta includes e_c (k = 2, 4 terms);
+//   diagonal: one group per term (k = 0).
+// Then <lam|P_T|psi> = phase_T * sum_x conj(lam[x]) psi[x^m] (-1)^popcount(zeta & x)
+//                      (-1)^popcount(s_T & u(x)), u(x) = bits of x at the support.
+int ensure_grad_groups(const syk_terms* t) {
+  SYK_TRY(ensure_device_tables(t));
+  std::lock_guard<std::mutex> lock(t->mtx);
+  if (t->d_gg_rec) return SYK_OK;
+  const int n = t->n, N = t->N;
+  const uint64_t Dmask = uint64_t(t->D) - 1;
+  std::map<std::pair<uint64_t, uint64_t>, int> key2g;
+  t->gg_rec.clear();
+  t->term_group.assign(t->nterms, -1);
+  t->term_s.assign(t->nterms, 0);
+  t->term_phase.assign(2 * t->nterms, 0.0);
+  int64_t T = 0;
+  for (int a = 0; a < N; ++a)
+    for (int b = a + 1; b < N; ++b)
+      for (int c = b + 1; c < N; ++c)
+        for (int d = c + 1; d < N; ++d, ++T) {
+          const uint64_t m = t->xm[T], z = t->zm[T];
+          const int pc = __builtin_popcountll(m);
+          uint64_t zeta, supp, keyz;
+          if (pc == 4) {
+            supp = m;
+            zeta = z & ~m;
+            keyz = 0;
+          } else if (pc == 2) {
+            const int sa = a / 2, sb = b / 2, sc = c / 2, sd = d / 2;
+            const int dbl = sa == sb ? sa : sb == sc ? sb : sd;
+            supp = m;
+            zeta = (z ^ (uint64_t(1) << dbl)) & ~m;
+            keyz = uint64_t(1) << dbl;
+          } else {
+            supp = 0;
+            zeta = z;
+            keyz = z;
+          }
+          const auto key = std::make_pair(m, keyz);
+          auto it = key2g.find(key);
+          int g;
+          if (it == key2g.end()) {
+            g = int(key2g.size());
+            key2g.emplace(key, g);
+            int pos[4] = {0, 0, 0, 0}, o = 0;
+            for (int k = 0; k < n; ++k)
+              if ((supp >> k) & 1) pos[o++] = k;
+            uint32_t shifts = 0;
+            for (int k = 0; k < 4; ++k) shifts |= uint32_t(k < o ? pos[k] - k : 31) << (8 * k);
+            t->gg_rec.insert(t->gg_rec.end(), {uint32_t(m & Dmask), uint32_t(zeta), shifts, uint32_t(o)});
+          } else {
+            g = it->second;
+          }
+          const uint64_t zs = pc == 2 ? (z ^ keyz) : z;
+          t->term_group[T] = g;
+          t->term_s[T] = uint8_t(syk::extract_bits(zs, supp));
+          std::complex<double> ph = syk::ipow(t->ph[T]) / 4.0;
+          if (__builtin_popcountll(z & m) & 1) ph = -ph;
+          t->term_phase[2 * T] = ph.real();
+          t->term_phase[2 * T + 1] = ph.imag();
+        }
+  t->ngg = int(key2g.size());
+  SYK_TRY(upload(&t->d_gg_rec, t->gg_rec.data(), t->gg_rec.size() * 4));
+  SYK_TRY(upload(&t->d_term_group, t->term_group.data(), t->term_group.size() * 4));
+  SYK_TRY(upload(&t->d_term_s, t->term_s.data(), t->term_s.size()));
+  SYK_TRY(upload(&t->d_term_phase, t->term_phase.data(), t->term_phase.size() * 8));
+  return SYK_OK;
+}
+
 
 }  // namespace syk

@@ -61,6 +61,8 @@ def load(build_if_missing: bool = False):
         "syk_profile_enable": (i32, [i32]),
         "syk_profile_read": (i32, [vp, vp, i32]),
         "syk_autotune_apply": (i32, [vp, i32, i32, i64, i32, vp, vp]),
+        "syk_otoc_grad": (i32, [vp, dbl, i32, i32, dbl, vp, i64, i32, i32, dbl, dbl, vp, vp, vp, vp]),
+        "syk_correlator_G_grad": (i32, [vp, dbl, i32, dbl, vp, i64, i32, i32, dbl, dbl, vp, vp, vp, vp]),
         "syk_autotune_export": (i32, [ctypes.c_char_p, sz]),
         "syk_autotune_import": (i32, [ctypes.c_char_p]),
     }
@@ -77,7 +79,8 @@ def exported_symbols():
     return ["syk_build_terms", "syk_free_terms", "syk_terms_info", "syk_term_table", "syk_apply_H",
             "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_expmv_static", "syk_correlator_G",
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
-            "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import"]
+            "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
+            "syk_correlator_G_grad"]
 
 
 def _check(rc: int, what: str):
@@ -289,3 +292,33 @@ def syk_autotune_export() -> str:
 
 def syk_autotune_import(text: str):
     _check(load().syk_autotune_import(text.encode()), "syk_autotune_import")
+
+
+def syk_otoc_grad(terms: Terms, beta: float, i: int, j: int, t: float, psi0, krylov_dim: int = 40,
+                  tol: float = 1e-12, quad_dz: float = 0.25, stream=None):
+    """Returns (F~(t) (B,), dF~/dJ (C(N,4), B), dF~/dbeta (B,)) as complex numpy arrays."""
+    ptr, B, code, keep = _input_ptr(psi0)
+    F = np.zeros((B, 2))
+    dJ = np.zeros((terms.nterms, B, 2))
+    db = np.zeros((B, 2))
+    _check(load().syk_otoc_grad(terms.ptr, float(beta), int(i), int(j), float(t), ptr, B, code, int(krylov_dim),
+                                float(tol), float(quad_dz), F.ctypes.data, dJ.ctypes.data, db.ctypes.data,
+                                _stream(stream)), "syk_otoc_grad")
+    del keep
+    c = lambda a: a[..., 0] + 1j * a[..., 1]
+    return c(F), c(dJ), c(db)
+
+
+def syk_correlator_G_grad(terms: Terms, beta: float, i: int, t: float, psi0, krylov_dim: int = 30,
+                          tol: float = 1e-12, quad_dz: float = 0.25, stream=None):
+    """Returns (G(t) (B,), dG/dJ (C(N,4), B), dG/dbeta (B,)) as complex numpy arrays."""
+    ptr, B, code, keep = _input_ptr(psi0)
+    G = np.zeros((B, 2))
+    dJ = np.zeros((terms.nterms, B, 2))
+    db = np.zeros((B, 2))
+    _check(load().syk_correlator_G_grad(terms.ptr, float(beta), int(i), float(t), ptr, B, code, int(krylov_dim),
+                                        float(tol), float(quad_dz), G.ctypes.data, dJ.ctypes.data, db.ctypes.data,
+                                        _stream(stream)), "syk_correlator_G_grad")
+    del keep
+    c = lambda a: a[..., 0] + 1j * a[..., 1]
+    return c(G), c(dJ), c(db)

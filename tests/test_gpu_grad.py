@@ -1,0 +1,70 @@
+"""Gradients of F~(t) and G(t) w.r.t. every coupling and beta on the GPU."""
+import numpy as np
+import pytest
+
+from helpers import rel, to_dev, torch_or_skip
+from oracle import gradient as gr
+from paper_2002_05725_gb300 import inputs, syk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = torch_or_skip()
+    syk.load(build_if_missing=True)
+    return t
+
+
+@pytest.mark.parametrize("N", [8, 12])
+def test_otoc_grad_vs_daleckii_krein(torch, N):
+    J = inputs.couplings(N, 5) * (2.0 if N == 8 else 1.0)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 2, 9)
+    beta, t, i, j = 3.0, 2.2, 0, 1
+    F, dJ, db = syk.syk_otoc_grad(terms, beta, i, j, t, to_dev(torch, psi, "c128"), krylov_dim=30, tol=1e-13,
+                                  quad_dz=0.1)
+    Fr, dJr, dbr = gr.otoc_tilde_grad(N, J, beta, i, j, t, psi.T)
+    assert rel(F, Fr) < 1e-11
+    assert rel(dJ, dJr) < 1e-8
+    assert rel(db, dbr) < 1e-8 * max(1.0, np.abs(dJr).max() / max(np.abs(dbr).max(), 1e-30))
+
+
+@pytest.mark.parametrize("N", [8, 12])
+def test_G_grad_vs_daleckii_krein(torch, N):
+    J = inputs.couplings(N, 6) * (2.0 if N == 8 else 1.0)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 3, 2)
+    beta, t, i = 2.0, 3.1, 3
+    G, dJ, db = syk.syk_correlator_G_grad(terms, beta, i, t, to_dev(torch, psi, "c128"), krylov_dim=30, tol=1e-13,
+                                          quad_dz=0.1)
+    Gr, dJr, dbr = gr.g_grad(N, J, beta, i, t, psi.T)
+    assert rel(G, Gr) < 1e-11
+    assert rel(dJ, dJr) < 1e-8
+    assert np.abs(db - dbr).max() < 1e-8 * max(np.abs(dJr).max(), np.abs(dbr).max())
+
+
+def test_otoc_grad_N28_finite_differences(torch):
+    """N = 28 (20475 couplings), beta J = 5, t* = 5: central differences (h = 1e-6) of the
+    GPU F~ on sampled couplings and beta, within 1e-4 relative; c64 gradient vs c128."""
+    N, beta, t = 28, 5.0, 5.0
+    J = inputs.couplings(N, 0)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 2, 0)
+    dev = to_dev(torch, psi, "c128")
+    F, dJ, db = syk.syk_otoc_grad(terms, beta, 0, 1, t, dev, krylov_dim=40, tol=1e-13, quad_dz=0.25)
+
+    def Ftil(Jx, b):
+        tx = syk.syk_build_terms(N, Jx)
+        Fx = syk.syk_otoc(tx, b, 0, 1, [0.0, t], dev, krylov_dim=40, tol=1e-13)
+        return Fx[1] / Fx[0]
+
+    rng = np.random.default_rng(28)
+    sample = rng.choice(len(J), 6, replace=False)
+    fdJ, fdb = gr.fd_grad(Ftil, J, beta, sample, h=1e-6)
+    scale = np.abs(dJ).max()
+    assert np.abs(dJ[sample] - fdJ).max() < 1e-4 * scale
+    assert np.abs(db - fdb).max() < 1e-4 * max(np.abs(db).max(), scale)
+    F64, dJ64, db64 = syk.syk_otoc_grad(terms, beta, 0, 1, t, to_dev(torch, psi, "c64"), krylov_dim=40, tol=1e-7,
+                                        quad_dz=0.25)
+    assert rel(dJ64, dJ) < 1e-4
