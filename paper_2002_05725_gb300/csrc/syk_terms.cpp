@@ -434,7 +434,7 @@ int tile_groups(const syk_terms* t, int tb, int gmax, const int4** out, int* cou
 // (P_T psi)[x] = (i^p/4) (-1)^popcount(z_T & (x^m)) psi[x^m].  Terms are grouped so that
 // z_T = zeta ^ spread(s_T) with s_T the bits of z_T at k "support" positions:
 //   popcount-4 masks: the 4 spins of m (k = 4, 16 terms);
-//   popcount-2 masks: one group per (m, doubled spin c), zeta includes e_c (k = 2, 4 terms);
+//   popcount-2 masks: one group per (m, doubled spin c) (k = 2, 4 terms);
 //   diagonal: one group per term (k = 0).
 // Then <lam|P_T|psi> = phase_T * sum_x conj(lam[x]) psi[x^m] (-1)^popcount(zeta & x)
 //                      (-1)^popcount(s_T & u(x)), u(x) = bits of x at the support.
@@ -465,7 +465,7 @@ int ensure_grad_groups(const syk_terms* t) {
             const int sa = a / 2, sb = b / 2, sc = c / 2, sd = d / 2;
             const int dbl = sa == sb ? sa : sb == sc ? sb : sd;
             supp = m;
-            zeta = (z ^ (uint64_t(1) << dbl)) & ~m;
+            zeta = z & ~m;  // shared by the 4 terms of (m, dbl), including the doubled spin's Z bit
             keyz = uint64_t(1) << dbl;
           } else {
             supp = 0;
@@ -487,9 +487,8 @@ int ensure_grad_groups(const syk_terms* t) {
           } else {
             g = it->second;
           }
-          const uint64_t zs = pc == 2 ? (z ^ keyz) : z;
           t->term_group[T] = g;
-          t->term_s[T] = uint8_t(syk::extract_bits(zs, supp));
+          t->term_s[T] = uint8_t(syk::extract_bits(z, supp));
           std::complex<double> ph = syk::ipow(t->ph[T]) / 4.0;
           if (__builtin_popcountll(z & m) & 1) ph = -ph;
           t->term_phase[2 * T] = ph.real();
