@@ -68,3 +68,20 @@ def test_otoc_grad_N28_finite_differences(torch):
     F64, dJ64, db64 = syk.syk_otoc_grad(terms, beta, 0, 1, t, to_dev(torch, psi, "c64"), krylov_dim=40, tol=1e-7,
                                         quad_dz=0.25)
     assert rel(dJ64, dJ) < 1e-4
+
+
+def test_autograd_function_matches_jacobian(torch):
+    from paper_2002_05725_gb300 import autograd as sa
+    N = 12
+    Jn = inputs.couplings(N, 2)
+    psi = to_dev(torch, inputs.random_states(N, 3, 4), "c128")
+    J = torch.tensor(Jn, dtype=torch.float64, requires_grad=True)
+    beta = torch.tensor(2.0, dtype=torch.float64, requires_grad=True)
+    out = sa.otoc_tilde(J, beta, N, 0, 1, 1.5, psi, krylov_dim=30, quad_dz=0.2)
+    w = torch.tensor([[1.0, -0.5], [0.25, 2.0], [-1.0, 0.3]], dtype=torch.float64)
+    (out * w).sum().backward()
+    _, dJ, db = gr.otoc_tilde_grad(N, Jn, 2.0, 0, 1, 1.5, psi.cpu().numpy())
+    refJ = dJ.real @ w[:, 0].numpy() + dJ.imag @ w[:, 1].numpy()
+    refb = float(db.real @ w[:, 0].numpy() + db.imag @ w[:, 1].numpy())
+    assert np.abs(J.grad.numpy() - refJ).max() < 1e-8 * np.abs(refJ).max()
+    assert abs(beta.grad.item() - refb) < 1e-8 * max(1.0, abs(refb))
