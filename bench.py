@@ -121,7 +121,8 @@ def applies_model(N, beta, times, m=40, tol=1e-7):
     total = applies(beta / 8) + applies(beta / 4)
     prev = 0.0
     for t in times:
-        total += 2 * applies(t - prev) + 2 * applies(t) + 2 * applies(beta / 4)
+        # forward increments of both chains, then rho^{1/4} U(t)^dag as one evolution of |z|
+        total += 2 * applies(t - prev) + 2 * applies(math.hypot(t, beta / 4))
         prev = t
     return total
 

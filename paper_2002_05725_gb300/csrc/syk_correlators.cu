@@ -183,12 +183,11 @@ extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const
     }
     SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, ua, pr, B, st));  // p (odd)
     SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, ub, qs, B, st));  // q (even)
-    if (tk > 0.0) {
-      SYK_TRY(expmv_impl(P1, dtype, {0.0, tk}, pr, pr, B, tol, ws, st, nullptr));  // U^dag p
-      SYK_TRY(expmv_impl(P0, dtype, {0.0, tk}, qs, qs, B, tol, ws, st, nullptr));  // U^dag q
-    }
-    SYK_TRY(expmv_impl(P1, dtype, q4, pr, pr, B, tol, ws, st, nullptr));  // r
-    SYK_TRY(expmv_impl(P0, dtype, q4, qs, qs, B, tol, ws, st, nullptr));  // s
+    // r = rho^{1/4} U^dag p and s = rho^{1/4} U^dag q: the two exponentials commute, so each
+    // is one Krylov evolution with z = -beta/4 + i t
+    const std::complex<double> zb(-beta / 4.0, tk);
+    SYK_TRY(expmv_impl(P1, dtype, zb, pr, pr, B, tol, ws, st, nullptr));  // r (odd)
+    SYK_TRY(expmv_impl(P0, dtype, zb, qs, qs, B, tol, ws, st, nullptr));  // s (even)
     SYK_TRY(launch_apply_chi(terms->N, j, 0, dtype, qs, tmp, B, st));     // chi_j s (odd)
     SYK_TRY(dot_columns(pr, tmp, terms->D, B, dtype, ws, r + size_t(k) * B, st));
   }

@@ -511,6 +511,10 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
   // complex64 vectors carry ~1e-7 relative error, which one reorthogonalisation pass already
   // reaches; complex128 vectors get the second pass ("twice is enough")
   const bool two_pass = dtype == SYK_C128;
+  // Convergence of the sub-step is checked after 4 vectors and then every `every` vectors: a
+  // check (eigensolve of T + one host read) costs far less than a matvec once the state is
+  // large, so large states are checked every 2 vectors, small ones every 8.
+  const int every = (double(ws.D) * double(B) >= double(1 << 18)) ? 2 : 8;
   const double zr = z.real(), zi = z.imag();
   int* hstat = static_cast<int*>(ws.host_stage ? ws.host_stage : pinned_scratch(64));
   double* hs = reinterpret_cast<double*>(hstat + 4);
@@ -546,7 +550,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
       count_launch();
       if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
       const bool last = (j + 1 == m);
-      if (last || j + 1 == 4 || ((j + 1) % 8 == 0)) {
+      if (last || j + 1 == 4 || (j + 1 > 4 && (j + 1) % every == 0)) {
         const int mm = j + 1;
         const size_t smem = sizeof(double) * (size_t(mm) * mm + 2 * mm + 2);
         k_tridiag_eig<<<int(B), 32, smem, st>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem,
