@@ -168,6 +168,25 @@ int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t,
              const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
              double* F_re_im, void* stream);
 
+/* syk_otoc_batch -- the batched workload: many independent OTOC evaluations
+ * (coupling draws of any N, each with its beta and its D x nstates random
+ * states, device or host memory) at the common times t, Majoranas i, j, dtype
+ * and Krylov settings.  Items are taken in order by `nworkers` host threads,
+ * each with its own CUDA stream, so that items of small sectors run
+ * concurrently; every distinct (N, nstates) is autotuned first.  Each item's
+ * F_re_im (host, nt x nstates x 2) is filled as by syk_otoc; item_status (may
+ * be NULL) receives each item's return code.  Returns the first failure.
+ * The paper averages over hundreds of such draws (Supp. Sec. I.C). */
+typedef struct {
+  const syk_terms* terms;
+  double beta;
+  const void* psi0;
+  int64_t nstates;
+  double* F_re_im;
+} syk_otoc_item;
+int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const double* t, int nt,
+                   int dtype, int krylov_dim, double tol, int nworkers, int* item_status);
+
 /* --------------------------------------------------------------- gradients
  * syk_otoc_grad -- F~(t) = F(t)/F(0) of syk_otoc at one time t for each state,
  * with its derivatives with respect to every coupling J_ijkl (Eq. 1) and beta.

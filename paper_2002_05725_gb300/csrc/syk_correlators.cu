@@ -5,8 +5,13 @@
 // batch dimension carries the random states of one coupling draw.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "syk_krylov.cuh"
@@ -139,15 +144,10 @@ extern "C" int syk_correlator_G(const syk_terms* terms, double beta, int i, cons
   return SYK_OK;
 }
 
-extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t, int nt, const void* psi0,
-                        int64_t nstates, int dtype, int krylov_dim, double tol, double* F_re_im, void* stream) {
-  clear_error();
-  SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im));
-  if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
-    set_error("syk_otoc: need 0 <= i != j < N (i=%d j=%d)", i, j);
-    return SYK_EINVAL;
-  }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+namespace syk {
+// Regularized OTOC of one coupling draw on stream st (arguments already validated).
+int otoc_impl(const syk_terms* terms, double beta, int i, int j, const double* t, int nt, const void* psi0,
+              int64_t nstates, int dtype, int krylov_dim, double tol, double* F_re_im, cudaStream_t st) {
   const int64_t B = nstates;
   ApplyParams P0, P1;
   SYK_TRY(make_apply_params(terms, 0, dtype, &P0));
@@ -200,4 +200,90 @@ extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const
     F_re_im[2 * e + 1] = h[e].y;
   }
   return SYK_OK;
+}
+}  // namespace syk
+
+extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t, int nt, const void* psi0,
+                        int64_t nstates, int dtype, int krylov_dim, double tol, double* F_re_im, void* stream) {
+  clear_error();
+  SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im));
+  if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
+    set_error("syk_otoc: need 0 <= i != j < N (i=%d j=%d)", i, j);
+    return SYK_EINVAL;
+  }
+  return otoc_impl(terms, beta, i, j, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im,
+                   static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------- batched workload
+// Independent work items (coupling draws of any N, with their beta and states) are taken
+// from a shared counter by `nworkers` host threads, each driving its own non-blocking CUDA
+// stream, so items of small sectors run concurrently and fill the GPU together.  Each
+// distinct (N, dtype, batch) is autotuned first on the calling thread.
+extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const double* t, int nt,
+                              int dtype, int krylov_dim, double tol, int nworkers, int* item_status) {
+  clear_error();
+  if (!items || nitems < 1 || nworkers < 1) {
+    set_error("syk_otoc_batch: need items, nitems >= 1 and nworkers >= 1");
+    return SYK_EINVAL;
+  }
+  for (int k = 0; k < nitems; ++k) {
+    const syk_otoc_item& it = items[k];
+    SYK_TRY(check_common(it.terms, it.beta, t, nt, it.psi0, it.nstates, dtype, krylov_dim, tol, it.F_re_im));
+    if (i < 0 || i >= it.terms->N || j < 0 || j >= it.terms->N || i == j) {
+      set_error("syk_otoc_batch: item %d: need 0 <= i != j < N", k);
+      return SYK_EINVAL;
+    }
+  }
+  int dev = 0;
+  SYK_CUDA_CHECK(cudaGetDevice(&dev));
+  // tune the matvec shape of every distinct (N, batch) once
+  {
+    std::vector<std::pair<int, int64_t>> done;
+    for (int k = 0; k < nitems; ++k) {
+      const auto key = std::make_pair(items[k].terms->N, items[k].nstates);
+      if (std::find(done.begin(), done.end(), key) != done.end()) continue;
+      done.push_back(key);
+      const int64_t b = items[k].nstates;
+      if ((b == 1 || b == 2 || b == 4 || b == 8 || b == 16) && items[k].terms->D >= 4096)
+        SYK_TRY(syk_autotune_apply(items[k].terms, 0, dtype, b, 2, nullptr, nullptr));
+    }
+  }
+  std::atomic<int> next{0};
+  std::mutex err_mtx;
+  int first_rc = SYK_OK;
+  std::string first_msg;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(err_mtx);
+      if (first_rc == SYK_OK) {
+        first_rc = SYK_ECUDA;
+        first_msg = "syk_otoc_batch: cannot create a stream";
+      }
+      return;
+    }
+    for (int k = next++; k < nitems; k = next++) {
+      const syk_otoc_item& it = items[k];
+      const int rc = otoc_impl(it.terms, it.beta, i, j, t, nt, it.psi0, it.nstates, dtype, krylov_dim, tol,
+                               it.F_re_im, st);
+      if (item_status) item_status[k] = rc;
+      if (rc != SYK_OK) {
+        std::lock_guard<std::mutex> lk(err_mtx);
+        if (first_rc == SYK_OK) {
+          first_rc = rc;
+          first_msg = std::string("item ") + std::to_string(k) + ": " + syk_last_error();
+        }
+      }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> pool;
+  const int nw = std::min(nworkers, nitems);
+  for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  if (first_rc != SYK_OK) set_error("syk_otoc_batch: %s", first_msg.c_str());
+  return first_rc;
 }

@@ -61,6 +61,7 @@ def load(build_if_missing: bool = False):
         "syk_profile_enable": (i32, [i32]),
         "syk_profile_read": (i32, [vp, vp, i32]),
         "syk_autotune_apply": (i32, [vp, i32, i32, i64, i32, vp, vp]),
+        "syk_otoc_batch": (i32, [vp, i32, i32, i32, vp, i32, i32, i32, dbl, i32, vp]),
         "syk_otoc_grad": (i32, [vp, dbl, i32, i32, dbl, vp, i64, i32, i32, dbl, dbl, vp, vp, vp, vp]),
         "syk_correlator_G_grad": (i32, [vp, dbl, i32, dbl, vp, i64, i32, i32, dbl, dbl, vp, vp, vp, vp]),
         "syk_autotune_export": (i32, [ctypes.c_char_p, sz]),
@@ -80,7 +81,7 @@ def exported_symbols():
             "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_expmv_static", "syk_correlator_G",
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
-            "syk_correlator_G_grad"]
+            "syk_correlator_G_grad", "syk_otoc_batch"]
 
 
 def _check(rc: int, what: str):
@@ -322,3 +323,33 @@ def syk_correlator_G_grad(terms: Terms, beta: float, i: int, t: float, psi0, kry
     del keep
     c = lambda a: a[..., 0] + 1j * a[..., 1]
     return c(G), c(dJ), c(db)
+
+
+class _OtocItem(ctypes.Structure):
+    _fields_ = [("terms", ctypes.c_void_p), ("beta", ctypes.c_double), ("psi0", ctypes.c_void_p),
+                ("nstates", ctypes.c_int64), ("F_re_im", ctypes.c_void_p)]
+
+
+def syk_otoc_batch(items, i: int, j: int, times, dtype: int = SYK_C64, krylov_dim: int = 40, tol: float = 1e-7,
+                   nworkers: int = 4):
+    """items: list of (Terms, beta, psi0) with psi0 a (D, B) CUDA tensor, host tensor or numpy array.
+
+    Returns a list of complex arrays F (nt, B), one per item.
+    """
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    keep, outs = [], []
+    arr = (_OtocItem * len(items))()
+    for k, (terms, beta, psi0) in enumerate(items):
+        ptr, B, code, kp = _input_ptr(psi0)
+        if code != dtype:
+            raise SykError("every item must use the batch dtype")
+        F = np.zeros((len(t), B, 2))
+        keep.append((kp, terms))
+        outs.append(F)
+        arr[k] = _OtocItem(terms.ptr.value, float(beta), ptr, B, F.ctypes.data)
+    status = np.zeros(len(items), dtype=np.int32)
+    _check(load().syk_otoc_batch(ctypes.cast(arr, ctypes.c_void_p), len(items), int(i), int(j), t.ctypes.data,
+                                 len(t), int(dtype), int(krylov_dim), float(tol), int(nworkers),
+                                 status.ctypes.data), "syk_otoc_batch")
+    del keep
+    return [F[..., 0] + 1j * F[..., 1] for F in outs]
