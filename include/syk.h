@@ -244,6 +244,11 @@ int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int64_t* launches, i
  * the device).  Reading returns launches and total milliseconds; reset != 0
  * zeroes them. */
 int syk_profile_enable(int on);
+/* syk_use_graphs -- on (default) / off: replay the Lanczos iterations between two
+ * convergence checks as captured CUDA graphs (per host thread, per workspace;
+ * graphs are rebuilt after term sets are freed or tile shapes retuned).  Graphs
+ * are not used while profiling is enabled. */
+int syk_use_graphs(int on);
 int syk_profile_read(int64_t* launches, double* total_ms, int reset);
 
 #ifdef __cplusplus

@@ -64,6 +64,7 @@ static bool tile_choice_lookup(int N, int dtype, int64_t batch, TileChoice* out)
 static void tile_choice_set(int N, int dtype, int64_t batch, TileChoice c) {
   std::lock_guard<std::mutex> lk(g_tune_mtx);
   g_tune[tune_key(N, dtype, batch)] = c;
+  bump_graph_epoch();  // captured matvec launches carry the old tile shape
 }
 
 namespace {

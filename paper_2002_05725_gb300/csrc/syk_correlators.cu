@@ -216,8 +216,8 @@ extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const
 }
 
 // ---------------------------------------------------------------- batched workload
-// Independent work items (coupling draws of any N, with their beta and states) are taken
-// from a shared counter by `nworkers` host threads, each driving its own non-blocking CUDA
+// Independent work items (coupling draws of any N, with their beta and states) are taken,
+// largest first, from a shared counter by `nworkers` host threads, each driving its own non-blocking CUDA
 // stream, so items of small sectors run concurrently and fill the GPU together.  Each
 // distinct (N, dtype, batch) is autotuned first on the calling thread.
 extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const double* t, int nt,
@@ -249,6 +249,12 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
         SYK_TRY(syk_autotune_apply(items[k].terms, 0, dtype, b, 2, nullptr, nullptr));
     }
   }
+  // largest items first (state size x states), so the long ones do not form the tail
+  std::vector<int> order(nitems);
+  for (int k = 0; k < nitems; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return double(items[a].terms->D) * items[a].nstates > double(items[b].terms->D) * items[b].nstates;
+  });
   std::atomic<int> next{0};
   std::mutex err_mtx;
   int first_rc = SYK_OK;
@@ -264,7 +270,8 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
       }
       return;
     }
-    for (int k = next++; k < nitems; k = next++) {
+    for (int q = next++; q < nitems; q = next++) {
+      const int k = order[q];
       const syk_otoc_item& it = items[k];
       const int rc = otoc_impl(it.terms, it.beta, i, j, t, nt, it.psi0, it.nstates, dtype, krylov_dim, tol,
                                it.F_re_im, st);

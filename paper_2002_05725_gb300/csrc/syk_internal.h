@@ -86,6 +86,14 @@ void prof_collect();
 void count_applies(int64_t states);
 void count_bases(int64_t n);
 void count_launch(int64_t n = 1);
+// While a thread captures a CUDA graph its counts go to thread-local tallies (returned by
+// capture_counts_end) so that every replay can add them.
+void capture_counts_begin();
+void capture_counts_end(int64_t* launches, int64_t* applies);
+bool prof_enabled();
+uint64_t graph_epoch();  // changes whenever captured graphs may hold stale parameters
+void bump_graph_epoch();
+bool graphs_enabled();
 
 inline size_t dtype_size(int dtype) { return dtype == SYK_C64 ? 8 : 16; }
 inline bool dtype_ok(int dtype) { return dtype == SYK_C64 || dtype == SYK_C128; }

@@ -13,7 +13,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <set>
+#include <tuple>
 
 #include "syk_cplx.cuh"
 #include "syk_krylov.cuh"
@@ -501,6 +504,81 @@ int dot_columns(const void* x, const void* y, int64_t D, int64_t B, int dtype, K
 // ---------------------------------------------------------------- expmv
 namespace {
 
+// Replays the kernel sequence of one Lanczos segment as a captured CUDA graph.  Graphs are
+// cached per host thread and keyed by everything their launches bake in (workspace, term
+// tables, sector, shapes, segment range) plus an epoch that changes when term sets are freed
+// or tile shapes retuned.  The first sighting of a key runs eagerly (lazy allocations happen
+// outside capture); the second captures and instantiates; later ones only launch.
+struct SegKey {
+  const void* V;
+  const void* tab;
+  int sector, dtype;
+  int64_t B, D;
+  int m, j0, j1, two;
+  uint64_t epoch;
+  bool operator<(const SegKey& o) const {
+    return std::tie(V, tab, sector, dtype, B, D, m, j0, j1, two, epoch) <
+           std::tie(o.V, o.tab, o.sector, o.dtype, o.B, o.D, o.m, o.j0, o.j1, o.two, o.epoch);
+  }
+};
+struct SegGraph {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0, applies = 0;
+};
+struct GraphCache {
+  std::map<SegKey, SegGraph> graphs;
+  std::set<SegKey> seen;
+  ~GraphCache() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+  }
+};
+thread_local GraphCache t_cache;
+
+template <typename F>
+int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int64_t B, int m, int j0, int j1,
+                        bool two, cudaStream_t st, F&& eager) {
+  if (!graphs_enabled() || prof_enabled()) return eager();
+  const SegKey key{ws.V, P.m4_tab, P.sector, dtype, B, P.D, m, j0, j1, two ? 1 : 0, graph_epoch()};
+  auto it = t_cache.graphs.find(key);
+  if (it == t_cache.graphs.end()) {
+    if (!t_cache.seen.count(key)) {
+      if (t_cache.seen.size() > 4096) t_cache.seen.clear();
+      t_cache.seen.insert(key);
+      return eager();
+    }
+    if (t_cache.graphs.size() > 512) {
+      for (auto& kv : t_cache.graphs) cudaGraphExecDestroy(kv.second.exec);
+      t_cache.graphs.clear();
+    }
+    SegGraph sg;
+    cudaGraph_t g = nullptr;
+    SYK_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    capture_counts_begin();
+    const int rc = eager();
+    capture_counts_end(&sg.launches, &sg.applies);
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (rc != SYK_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ec != cudaSuccess) {
+      set_error("expmv: graph capture failed: %s", cudaGetErrorString(ec));
+      return SYK_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&sg.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      set_error("expmv: graph instantiation failed: %s", cudaGetErrorString(ei));
+      return SYK_ECUDA;
+    }
+    it = t_cache.graphs.emplace(key, sg).first;
+  }
+  SYK_CUDA_CHECK(cudaGraphLaunch(it->second.exec, st));
+  count_launch(it->second.launches);
+  count_applies(it->second.applies);
+  return SYK_OK;
+}
+
 template <typename R>
 int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, void* out, double tol,
             KrylovWS& ws, cudaStream_t st, int* nsteps) {
@@ -534,24 +612,36 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
     count_launch();
     Ops<R>::scale(ws, cur, ws.vec(0), ws.inv, st);
     int m_eff = m;
-    for (int j = 0; j < m; ++j) {
-      SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, B, st));
-      // classical Gram-Schmidt against the whole basis; a second pass for FP64 vectors
-      Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
-      reduce_parts(ws, j + 1, ws.h1, st);
-      Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, two_pass ? nullptr : ws.npart, st);
-      if (two_pass) {
+    // Lanczos iterations j in [j0, j1) between two convergence checks
+    auto segment = [&](int j0, int j1) -> int {
+      for (int j = j0; j < j1; ++j) {
+        SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, B, st));
+        // classical Gram-Schmidt against the whole basis; a second pass for FP64 vectors
         Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
-        reduce_parts(ws, j + 1, ws.h2, st);
-        Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
+        reduce_parts(ws, j + 1, ws.h1, st);
+        Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, two_pass ? nullptr : ws.npart, st);
+        if (two_pass) {
+          Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
+          reduce_parts(ws, j + 1, ws.h2, st);
+          Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
+        }
+        k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, two_pass ? ws.h2 : nullptr,
+                                                                 ws.npart, ws.alpha, ws.beta, ws.inv, ws.status, bt);
+        count_launch();
+        if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
       }
-      k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, two_pass ? ws.h2 : nullptr,
-                                                               ws.npart, ws.alpha, ws.beta, ws.inv, ws.status, bt);
-      count_launch();
-      if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
-      const bool last = (j + 1 == m);
-      if (last || j + 1 == 4 || (j + 1 > 4 && (j + 1) % every == 0)) {
-        const int mm = j + 1;
+      SYK_CUDA_CHECK(cudaGetLastError());
+      return SYK_OK;
+    };
+    int j0 = 0;
+    while (j0 < m) {
+      int j1 = j0 + 1;
+      while (!(j1 == m || j1 == 4 || (j1 > 4 && j1 % every == 0))) ++j1;
+      SYK_TRY(run_segment_graphed(P, ws, dtype, B, m, j0, j1, two_pass, st, [&]() { return segment(j0, j1); }));
+      const int j = j1 - 1;
+      const bool last = (j1 == m);
+      {
+        const int mm = j1;
         const size_t smem = sizeof(double) * (size_t(mm) * mm + 2 * mm + 2);
         k_tridiag_eig<<<int(B), 32, smem, st>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem,
                                                 tol, ws.theta, ws.Q, ws.sb, ws.status);
@@ -579,6 +669,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
           break;
         }
       }
+      j0 = j1;
     }
     double s_acc = std::min(*hs, s_rem);
     if (!(s_acc > 1e-13 * s_rem) && !(s_acc >= s_rem)) {

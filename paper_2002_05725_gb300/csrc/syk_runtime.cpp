@@ -40,9 +40,38 @@ thread_local cudaEvent_t t_start = nullptr;
 
 }  // namespace
 
-void count_applies(int64_t states) { g_applies += states; }
+thread_local bool t_capturing = false;
+thread_local int64_t t_cap_launches = 0, t_cap_applies = 0;
+std::atomic<uint64_t> g_epoch{1};
+std::atomic<bool> g_graphs{true};
+
+void count_applies(int64_t states) {
+  if (t_capturing) t_cap_applies += states;
+  else g_applies += states;
+}
 void count_bases(int64_t n) { g_bases += n; }
-void count_launch(int64_t n) { g_launches += n; }
+void count_launch(int64_t n) {
+  if (t_capturing) t_cap_launches += n;
+  else g_launches += n;
+}
+void capture_counts_begin() {
+  t_capturing = true;
+  t_cap_launches = t_cap_applies = 0;
+}
+void capture_counts_end(int64_t* launches, int64_t* applies) {
+  t_capturing = false;
+  *launches = t_cap_launches;
+  *applies = t_cap_applies;
+}
+uint64_t graph_epoch() { return g_epoch.load(); }
+void bump_graph_epoch() { ++g_epoch; }
+bool graphs_enabled() { return g_graphs.load(); }
+
+bool prof_enabled() {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> lk(p.mtx);
+  return p.on;
+}
 
 void prof_before_apply(cudaStream_t st) {
   Prof& p = prof();
@@ -108,6 +137,12 @@ extern "C" int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int64_t* 
     syk::g_bases = 0;
     syk::g_launches = 0;
   }
+  return SYK_OK;
+}
+
+extern "C" int syk_use_graphs(int on) {
+  syk::g_graphs = on != 0;
+  syk::bump_graph_epoch();
   return SYK_OK;
 }
 

@@ -270,6 +270,7 @@ extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
 
 extern "C" void syk_free_terms(syk_terms* t) {
   if (!t) return;
+  syk::bump_graph_epoch();  // graphs may hold this term set's device pointers
   if (t->dev.device >= 0) {
     int prev = -1;
     cudaGetDevice(&prev);

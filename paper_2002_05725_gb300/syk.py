@@ -59,6 +59,7 @@ def load(build_if_missing: bool = False):
         "syk_last_error": (ctypes.c_char_p, []),
         "syk_counters": (i32, [vp, vp, vp, i32]),
         "syk_profile_enable": (i32, [i32]),
+        "syk_use_graphs": (i32, [i32]),
         "syk_profile_read": (i32, [vp, vp, i32]),
         "syk_autotune_apply": (i32, [vp, i32, i32, i64, i32, vp, vp]),
         "syk_otoc_batch": (i32, [vp, i32, i32, i32, vp, i32, i32, i32, dbl, i32, vp]),
@@ -81,7 +82,7 @@ def exported_symbols():
             "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_expmv_static", "syk_correlator_G",
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
-            "syk_correlator_G_grad", "syk_otoc_batch"]
+            "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs"]
 
 
 def _check(rc: int, what: str):
@@ -353,3 +354,7 @@ def syk_otoc_batch(items, i: int, j: int, times, dtype: int = SYK_C64, krylov_di
                                  status.ctypes.data), "syk_otoc_batch")
     del keep
     return [F[..., 0] + 1j * F[..., 1] for F in outs]
+
+
+def syk_use_graphs(on: bool = True):
+    _check(load().syk_use_graphs(int(on)), "syk_use_graphs")

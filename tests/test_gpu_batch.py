@@ -41,3 +41,23 @@ def test_otoc_batch_reports_item_errors():
     psi = np.zeros((32, 1), dtype=np.complex64)
     with pytest.raises(syk.SykError):
         syk.syk_otoc_batch([(terms, -1.0, psi)], 0, 1, [0.0], dtype=syk.SYK_C64)
+
+
+def test_graph_replay_matches_eager():
+    """Lanczos segments replayed from captured CUDA graphs give the same numbers as eager launches."""
+    torch = torch_or_skip()
+    syk.load(build_if_missing=True)
+    N = 16
+    terms = syk.syk_build_terms(N, inputs.couplings(N, 8))
+    x = to_dev(torch, inputs.random_states(N, 4, 8), "c128")
+    ts = [0.0, 0.5, 1.5, 4.0]
+    syk.syk_use_graphs(False)
+    eager = syk.syk_otoc(terms, 2.0, 0, 1, ts, x, krylov_dim=30, tol=1e-12)
+    syk.syk_use_graphs(True)
+    syk.syk_counters(reset=True)
+    g1 = syk.syk_otoc(terms, 2.0, 0, 1, ts, x, krylov_dim=30, tol=1e-12)   # captures within the call
+    c1 = syk.syk_counters(reset=True)
+    g2 = syk.syk_otoc(terms, 2.0, 0, 1, ts, x, krylov_dim=30, tol=1e-12)
+    c2 = syk.syk_counters(reset=True)
+    assert np.array_equal(g1, eager) and np.array_equal(g2, eager)
+    assert c1["h_applies"] == c2["h_applies"] and c1["launches"] == c2["launches"]
