@@ -528,6 +528,7 @@ struct SegGraph {
 struct GraphCache {
   std::map<SegKey, SegGraph> graphs;
   std::set<SegKey> seen;
+  cudaStream_t cap = nullptr;  // capture stream (the legacy default stream cannot be captured)
   ~GraphCache() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
   }
@@ -537,14 +538,14 @@ thread_local GraphCache t_cache;
 template <typename F>
 int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int64_t B, int m, int j0, int j1,
                         bool two, cudaStream_t st, F&& eager) {
-  if (!graphs_enabled() || prof_enabled()) return eager();
+  if (!graphs_enabled() || prof_enabled()) return eager(st);
   const SegKey key{ws.V, P.m4_tab, P.sector, dtype, B, P.D, m, j0, j1, two ? 1 : 0, graph_epoch()};
   auto it = t_cache.graphs.find(key);
   if (it == t_cache.graphs.end()) {
     if (!t_cache.seen.count(key)) {
       if (t_cache.seen.size() > 4096) t_cache.seen.clear();
       t_cache.seen.insert(key);
-      return eager();
+      return eager(st);
     }
     if (t_cache.graphs.size() > 512) {
       for (auto& kv : t_cache.graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -552,11 +553,12 @@ int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int
     }
     SegGraph sg;
     cudaGraph_t g = nullptr;
-    SYK_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    if (!t_cache.cap) SYK_CUDA_CHECK(cudaStreamCreateWithFlags(&t_cache.cap, cudaStreamNonBlocking));
+    SYK_CUDA_CHECK(cudaStreamBeginCapture(t_cache.cap, cudaStreamCaptureModeThreadLocal));
     capture_counts_begin();
-    const int rc = eager();
+    const int rc = eager(t_cache.cap);  // recorded, not executed
     capture_counts_end(&sg.launches, &sg.applies);
-    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    const cudaError_t ec = cudaStreamEndCapture(t_cache.cap, &g);
     if (rc != SYK_OK) {
       if (g) cudaGraphDestroy(g);
       return rc;
@@ -613,7 +615,7 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
     Ops<R>::scale(ws, cur, ws.vec(0), ws.inv, st);
     int m_eff = m;
     // Lanczos iterations j in [j0, j1) between two convergence checks
-    auto segment = [&](int j0, int j1) -> int {
+    auto segment = [&](int j0, int j1, cudaStream_t st) -> int {
       for (int j = j0; j < j1; ++j) {
         SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, B, st));
         // classical Gram-Schmidt against the whole basis; a second pass for FP64 vectors
@@ -637,7 +639,8 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
     while (j0 < m) {
       int j1 = j0 + 1;
       while (!(j1 == m || j1 == 4 || (j1 > 4 && j1 % every == 0))) ++j1;
-      SYK_TRY(run_segment_graphed(P, ws, dtype, B, m, j0, j1, two_pass, st, [&]() { return segment(j0, j1); }));
+      SYK_TRY(run_segment_graphed(P, ws, dtype, B, m, j0, j1, two_pass, st,
+                                  [&](cudaStream_t s) { return segment(j0, j1, s); }));
       const int j = j1 - 1;
       const bool last = (j1 == m);
       {
