@@ -254,6 +254,23 @@ def config_dict(a, times):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(value, device, world):
+    """Largest value over the ranks (timing is the slowest rank's); no-op for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def curves_per_hour(world, states, steps, t_max_ms):
+    """Whole-job throughput: every rank evaluates `states` curves per step (weak scaling)."""
+    return world * states * steps * 3600.0 / (t_max_ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def gpu_main(a, rank, world, local_rank):
     import torch
@@ -311,12 +328,8 @@ def gpu_main(a, rank, world, local_rank):
     prof = syk.syk_profile_read(reset=True)
     cnt = syk.syk_counters(reset=True)
     barrier()
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * a.states * a.steps * 3600.0 / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, dev, world)
+    value = curves_per_hour(world, a.states, a.steps, t_max)
 
     # end to end: host (pinned) inputs through the C ABI, result read back to host
     e2e_ms = 0.0
@@ -326,12 +339,8 @@ def gpu_main(a, rank, world, local_rank):
         t0 = time.perf_counter()
         F = step(psi_host.numpy())
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_max = e2e_ms
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_max = float(t.item())
-    e2e_val = world * a.states * a.e2e_steps * 3600.0 / (e2e_max / 1e3) if a.e2e_steps else None
+    e2e_max = max_over_ranks(e2e_ms, dev, world)
+    e2e_val = curves_per_hour(world, a.states, a.e2e_steps, e2e_max) if a.e2e_steps else None
 
     if rank != 0:
         return
