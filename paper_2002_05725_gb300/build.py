@@ -34,21 +34,26 @@ def _inputs():
         [os.path.join(ROOT, "include", "syk.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = OUT_DIR) -> str:
+    """Builds the library into out_dir (default: the in-tree _build) and returns its path.
+
+    extra_flags are added to every nvcc compile (e.g. -DSYK_MASK_UNROLL=2 for a variant build
+    in another directory, loaded with SYK_LIBRARY=<path>)."""
+    lib = os.path.join(out_dir, "libsyk_gb300.so")
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         cmds.append([nvcc(), *ARCH, *NVCC_FLAGS, *extra_flags, "-I", os.path.join(ROOT, "include"),
                      "-c", src, "-o", obj])
@@ -65,12 +70,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for err in ex.map(run, cmds):
             if verbose and err:
                 print(err, file=sys.stderr)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
-                extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("--ptxas", action="store_true", help="print register and shared-memory use")
+    ap.add_argument("--out-dir", default=OUT_DIR)
+    ap.add_argument("-D", action="append", default=[], help="preprocessor definition for a variant build")
+    a = ap.parse_args()
+    flags = (["-Xptxas", "-v"] if a.ptxas else []) + [f"-D{d}" for d in a.D]
+    print(build(force=a.force, verbose=True, extra_flags=flags, out_dir=a.out_dir))

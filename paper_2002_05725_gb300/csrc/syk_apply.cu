@@ -41,6 +41,23 @@
 #include "syk_cplx.cuh"
 #include "syk_internal.h"
 
+// Unroll factor of the per-chunk mask loop of the tiled matvec (build-time knob).
+#ifndef SYK_MASK_UNROLL
+#define SYK_MASK_UNROLL 1
+#endif
+// Masks staged per chunk, and rows per thread of the 8- and 16-state complex64 kernels.
+#ifndef SYK_GMAX
+#define SYK_GMAX 16
+#endif
+#ifndef SYK_RPT_C64_B8
+#define SYK_RPT_C64_B8 2
+#endif
+#ifndef SYK_RPT_C64_B16
+#define SYK_RPT_C64_B16 1
+#endif
+#define SYK_PRAGMA(x) _Pragma(#x)
+#define SYK_UNROLL(n) SYK_PRAGMA(unroll n)
+
 namespace syk {
 
 // Tile configuration chosen by the autotuner per (N, dtype, batch): CTA width 2^ntb and
@@ -310,14 +327,14 @@ struct TileCfg {
   using C = typename CT<R>::T;
   // rows per thread: more rows share one table-index computation, fewer leave room
   // for more resident warps
-  static constexpr int RPT = sizeof(R) == 4 ? (BT == 1 ? 8 : BT <= 4 ? 4 : BT == 8 ? 2 : 1)
+  static constexpr int RPT = sizeof(R) == 4 ? (BT == 1 ? 8 : BT <= 4 ? 4 : BT == 8 ? SYK_RPT_C64_B8 : SYK_RPT_C64_B16)
                                             : (BT == 1 ? 4 : BT <= 4 ? 2 : 1);
   static constexpr int ROWB = BT * (int)sizeof(C);
   static constexpr int CH = ROWB >= 16 ? ROWB / 16 : 0;  // 16-byte chunks per row
   static constexpr int NS = CH ? CH : 1;
   // each buffer stages the partner tile plus the records and 32-entry coefficient
   // tables of up to GMAX popcount-4 masks
-  static constexpr int GMAX = 16;
+  static constexpr int GMAX = SYK_GMAX;
   static constexpr int TABB = 32 * (int)sizeof(C);
   static constexpr int AUXB = GMAX * (TABB + 16);
   static size_t buf_bytes(int T) { return (size_t)T * ROWB + AUXB; }
@@ -415,6 +432,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       const C* stab = reinterpret_cast<const C*>(tb + TILEB);
       const uint4* srec = reinterpret_cast<const uint4*>(tb + TILEB + GMAX * TABB);
       const int nm = gr.z - gr.y;
+      SYK_UNROLL(SYK_MASK_UNROLL)
       for (int kk = 0; kk < nm; ++kk) {
         const uint4 rec = srec[kk];
         const uint32_t lo = rec.x & (uint32_t)(T - 1);

@@ -28,7 +28,8 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library to load: $SYK_LIBRARY if set (a variant build), else the in-tree build."""
+    return os.environ.get("SYK_LIBRARY", _build.LIB)
 
 
 def load(build_if_missing: bool = False):
@@ -36,12 +37,13 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
-        if not build_if_missing:
-            raise SykError(f"CUDA library {_build.LIB} is not built; run __graft_entry__.build() "
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing or path != _build.LIB:
+            raise SykError(f"CUDA library {path} is not built; run __graft_entry__.build() "
                            "or python -m paper_2002_05725_gb300.build")
         _build.build()
-    L = ctypes.CDLL(_build.LIB)
+    L = ctypes.CDLL(path)
     vp, i64, i32, dbl, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     sig = {
         "syk_build_terms": (i32, [i32, vp, ctypes.POINTER(vp)]),
