@@ -50,10 +50,10 @@
 #define SYK_GMAX 16
 #endif
 #ifndef SYK_RPT_C64_B8
-#define SYK_RPT_C64_B8 2
+#define SYK_RPT_C64_B8 4
 #endif
 #ifndef SYK_RPT_C64_B16
-#define SYK_RPT_C64_B16 1
+#define SYK_RPT_C64_B16 2
 #endif
 #define SYK_PRAGMA(x) _Pragma(#x)
 #define SYK_UNROLL(n) SYK_PRAGMA(unroll n)
