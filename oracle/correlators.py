@@ -65,6 +65,74 @@ def F_state(sys: SectorSystem, beta: float, i: int, j: int, times, psi: np.ndarr
     return np.array(out)
 
 
+def F_state_split(sys: SectorSystem, beta: float, x, i: int, j: int, times, psi: np.ndarray):
+    """OTOC with a general split of rho = e^{-beta H} between the operators:
+
+      F(t) = Tr[W(t) rho^{x1} V rho^{x2} W(t) rho^{x3} V rho^{x4}],  x1+x2+x3+x4 = 1,
+
+    W = chi_i, V = chi_j (x = 1/4 each: Eq. F_reg; x = (0, 0, 0, 1): the unregularized
+    OTOC of Supp. Sec. unreg).  By cyclicity the one-state estimate (Eq. q_typicality) is
+    <psi~| rho^{x4/2} W rho^{x1} V rho^{x2} W rho^{x3} V rho^{x4/2} |psi~> = <r|chi_j|s> with
+      phi = rho^{x4/2} psi~,  a0 = rho^{x3} chi_j phi,
+      r = rho^{x1} U^dag chi_i U phi,  s = rho^{x2} U^dag chi_i U a0.
+    """
+    x1, x2, x3, x4 = x
+    phi = sys.expmv(-beta * x4 / 2.0, psi, 0)
+    a0 = sys.expmv(-beta * x3, sys.chi(j, 0, phi), 1)
+    out = []
+    for t in times:
+        p = sys.chi(i, 0, sys.expmv(-1j * t, phi, 0))
+        q = sys.chi(i, 1, sys.expmv(-1j * t, a0, 1))
+        r = sys.expmv(-beta * x1, sys.expmv(1j * t, p, 1), 1)
+        s = sys.expmv(-beta * x2, sys.expmv(1j * t, q, 0), 0)
+        out.append(_dot(r, sys.chi(j, 0, s)))
+    return np.array(out)
+
+
+def G_imag_state(sys: SectorSystem, beta: float, i: int, taus, psi: np.ndarray):
+    """Imaginary-time G(tau) = <chi_i(tau) chi_i(0)>_beta (Eq. G), chi(tau) = e^{tau H} chi e^{-tau H},
+    estimated as <psi~|e^{-beta H/2} chi_i(tau) chi_i e^{-beta H/2}|psi~> / <psi~|e^{-beta H}|psi~>
+    (Eq. q_typicality).  Returns (G[ntau(, B)], Z)."""
+    x = sys.expmv(-beta / 2.0, psi, 0)
+    Z = np.real(_dot(x, x))
+    out = []
+    for tau in taus:
+        w = sys.expmv(tau, x, 0)                                  # e^{(tau - beta/2) H} psi~
+        y = sys.expmv(-tau, sys.chi(i, 0, x), 1)                  # e^{-tau H} chi_i x
+        out.append(_dot(w, sys.chi(i, 1, y)) / Z)
+    return np.array(out), Z
+
+
+def G_imag_trace_even(N: int, J: np.ndarray, beta: float, i: int, taus):
+    """Tr[P_e e^{-beta H} chi_i(tau) chi_i] / Tr[P_e e^{-beta H}] from full dense matrices."""
+    H = H_dense(N, J)
+    Pe = _even_projector_full(N)
+    c = chi_dense(N, i)
+    R = sla.expm(-beta * H)
+    Z = np.trace(Pe @ R).real
+    out = []
+    for tau in taus:
+        ct = sla.expm(tau * H) @ c @ sla.expm(-tau * H)
+        out.append(np.trace(Pe @ sla.expm(-beta / 2 * H) @ ct @ c @ sla.expm(-beta / 2 * H)) / Z)
+    return np.array(out)
+
+
+def F_trace_split(N: int, J: np.ndarray, beta: float, x, i: int, j: int, times, sector=0):
+    """Tr[P rho^{x4/2} W(t) rho^{x1} V rho^{x2} W(t) rho^{x3} V rho^{x4/2}] (dense; P: sector projector)."""
+    H = H_dense(N, J)
+    P = _even_projector_full(N, sector)
+    W0 = chi_dense(N, i)
+    V = chi_dense(N, j)
+    rr = [sla.expm(-beta * xk * H) for xk in x]
+    rh = sla.expm(-beta * x[3] / 2 * H)
+    out = []
+    for t in times:
+        U = sla.expm(-1j * t * H)
+        W = U.conj().T @ W0 @ U
+        out.append(np.trace(P @ rh @ W @ rr[0] @ V @ rr[1] @ W @ rr[2] @ V @ rh))
+    return np.array(out)
+
+
 # ----------------------------------------------------------------------------- traces
 
 def _even_projector_full(N: int, sector=0) -> np.ndarray:

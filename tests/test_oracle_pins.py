@@ -271,3 +271,54 @@ def test_F_basis_sum_equals_trace_and_is_real():
     full = co.F_trace_even(N, J, 2.0, 1, 6, ts, sector=None)
     assert np.abs(full.imag).max() < 1e-14 * np.abs(full).max()
     assert np.abs(full - tr - co.F_trace_even(N, J, 2.0, 1, 6, ts, sector=1)).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------- regularization family, G(tau)
+
+@pytest.mark.parametrize("x", [(0.25, 0.25, 0.25, 0.25), (0.0, 0.0, 0.0, 1.0), (0.1, 0.4, 0.2, 0.3)])
+def test_F_split_N4_closed_form(x):
+    """N=4 even sector (H = -J/4 there, +J/4 in the odd sector): for every split of rho,
+    F(t) = -(1/4)|psi|^2 e^{beta J (x2 + x4 - x1 - x3)/4} e^{-iJt}, so F~(t) = e^{-iJt}."""
+    Jv, beta = 0.9, 2.3
+    sysm = evolve.SectorSystem(4, np.array([Jv]))
+    psi = inputs.random_states(4, 1, 5)[0]
+    ts = np.linspace(0, 6, 7)
+    F = co.F_state_split(sysm, beta, x, 0, 1, ts, psi)
+    nrm = np.vdot(psi, psi).real
+    ref = -0.25 * nrm * np.exp(beta * Jv * (x[1] + x[3] - x[0] - x[2]) / 4) * np.exp(-1j * Jv * ts)
+    assert np.abs(F - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_F_split_regularized_is_F_reg_and_basis_sum_is_trace():
+    N = 8
+    J = inputs.couplings(N, 12) * 3.0
+    sysm = evolve.SectorSystem(N, J)
+    psi = inputs.random_states(N, 2, 3).T
+    ts = [0.0, 0.9, 3.0]
+    assert np.abs(co.F_state_split(sysm, 2.0, (0.25,) * 4, 1, 6, ts, psi)
+                  - co.F_state(sysm, 2.0, 1, 6, ts, psi)).max() < 1e-13
+    x = (0.0, 0.0, 0.0, 1.0)
+    F = co.F_state_split(sysm, 2.0, x, 1, 6, ts, co.basis_states_even(N))
+    tr = co.F_trace_split(N, J, 2.0, x, 1, 6, ts)
+    assert np.abs(np.sum(F, axis=1) - tr).max() < 1e-12 * np.abs(tr).max()
+    # t = 0: chi_i chi_j chi_i chi_j = -1/4, so the full trace is -Tr[rho]/4
+    full = co.F_trace_split(N, J, 2.0, x, 1, 6, ts, sector=None)
+    assert abs(full[0] + 0.25 * np.trace(sla.expm(-2.0 * hm.H_dense(N, J))).real) < 1e-12
+
+
+def test_G_imag_N4_and_definitions():
+    """N=4: chi_0(tau) chi_0 = e^{2 tau H}/2, so G(tau) = e^{-J tau/2}/2 in the even sector;
+    G(0) = 1/2 at any N; the basis sum equals the dense trace form."""
+    Jv, beta = 0.8, 3.0
+    sysm = evolve.SectorSystem(4, np.array([Jv]))
+    psi = inputs.random_states(4, 1, 2)[0]
+    taus = np.linspace(0, beta, 5)
+    G, _ = co.G_imag_state(sysm, beta, 0, taus, psi)
+    assert np.abs(G - 0.5 * np.exp(-Jv * taus / 2)).max() < 1e-14
+    N = 8
+    J = inputs.couplings(N, 4) * 3.0
+    sysm = evolve.SectorSystem(N, J)
+    G, Z = co.G_imag_state(sysm, 2.0, 3, [0.0, 0.7, 2.0], co.basis_states_even(N))
+    assert np.abs(G[0] - 0.5).max() < 1e-14
+    est = np.sum(G * Z[None, :], axis=1) / np.sum(Z)
+    assert np.abs(est - co.G_imag_trace_even(N, J, 2.0, 3, [0.0, 0.7, 2.0])).max() < 1e-13
