@@ -168,6 +168,29 @@ int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t,
              const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
              double* F_re_im, void* stream);
 
+/* syk_otoc_split -- the OTOC family with a general split of rho = e^{-beta H}
+ * between the four operators (Supp. Sec. on unregularized OTOCs and on
+ * regularizations: reducing the imaginary-time separation of the operators):
+ *   F(t) = Tr[chi_i(t) rho^{x1} chi_j rho^{x2} chi_i(t) rho^{x3} chi_j rho^{x4}],
+ * x[0..3] >= 0 summing to 1; x = 1/4 each is syk_otoc (Eq. F_reg), x = (0,0,0,1)
+ * the unregularized OTOC <chi_i(t) chi_j chi_i(t) chi_j rho>.  One-state estimate
+ * (Eq. q_typicality) by the chain phi = rho^{x4/2} psi~, a0 = rho^{x3} chi_j phi,
+ * F = < rho^{x1} U^dag chi_i U phi | chi_j | rho^{x2} U^dag chi_i U a0 >.  Other
+ * conventions as syk_otoc. */
+int syk_otoc_split(const syk_terms* terms, double beta, const double* x, int i, int j, const double* t,
+                   int nt, const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
+                   double* F_re_im, void* stream);
+
+/* syk_correlator_G_imag -- imaginary-time two-point function, Eq. G:
+ * G(tau) = <chi_i(tau) chi_i(0)>_beta with chi(tau) = e^{tau H} chi e^{-tau H}, estimated
+ * (Eq. q_typicality) as <psi~|e^{-beta H/2} chi_i(tau) chi_i e^{-beta H/2}|psi~> / Z,
+ * Z = <psi~|e^{-beta H}|psi~>, for 0 <= tau (non-decreasing).  The factor
+ * e^{(tau - beta/2) H} grows for tau > beta/2, so the estimate loses digits like
+ * e^{(tau - beta/2) |E|}.  Conventions as syk_correlator_G. */
+int syk_correlator_G_imag(const syk_terms* terms, double beta, int i, const double* tau, int ntau,
+                          const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
+                          double* G_re_im, double* Z, void* stream);
+
 /* syk_otoc_batch -- the batched workload: many independent OTOC evaluations
  * (coupling draws of any N, each with its beta and its D x nstates random
  * states, device or host memory) at the common times t, Majoranas i, j, dtype

@@ -145,9 +145,13 @@ extern "C" int syk_correlator_G(const syk_terms* terms, double beta, int i, cons
 }
 
 namespace syk {
-// Regularized OTOC of one coupling draw on stream st (arguments already validated).
-int otoc_impl(const syk_terms* terms, double beta, int i, int j, const double* t, int nt, const void* psi0,
-              int64_t nstates, int dtype, int krylov_dim, double tol, double* F_re_im, cudaStream_t st) {
+// OTOC of one coupling draw on stream st (arguments already validated), with rho split as
+// Tr[W(t) rho^{x1} V rho^{x2} W(t) rho^{x3} V rho^{x4}] (x = 1/4 each: Eq. F_reg):
+//   phi = rho^{x4/2} psi~, a0 = rho^{x3} chi_j phi, p = chi_i U(t) phi, q = chi_i U(t) a0,
+//   F = < rho^{x1} U(t)^dag p | chi_j | rho^{x2} U(t)^dag q >.
+int otoc_impl(const syk_terms* terms, double beta, const double* x, int i, int j, const double* t, int nt,
+              const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol, double* F_re_im,
+              cudaStream_t st) {
   const int64_t B = nstates;
   ApplyParams P0, P1;
   SYK_TRY(make_apply_params(terms, 0, dtype, &P0));
@@ -168,11 +172,10 @@ int otoc_impl(const syk_terms* terms, double beta, int i, int j, const double* t
   KrylovWS ws;
   SYK_TRY(krylov_ws_carve(&ws, wsp, wsb, terms->D, dtype, krylov_dim, B));
   double2* r = static_cast<double2*>(res);
-  const std::complex<double> q8(-beta / 8.0, 0.0), q4(-beta / 4.0, 0.0);
-  // ua = phi = rho^{1/8} psi~ (even); ub = a0 = rho^{1/4} chi_j phi (odd)
-  SYK_TRY(expmv_impl(P0, dtype, q8, psi, ua, B, tol, ws, st, nullptr));
+  // ua = phi = rho^{x4/2} psi~ (even); ub = a0 = rho^{x3} chi_j phi (odd)
+  SYK_TRY(expmv_impl(P0, dtype, {-beta * x[3] / 2.0, 0.0}, psi, ua, B, tol, ws, st, nullptr));
   SYK_TRY(launch_apply_chi(terms->N, j, 0, dtype, ua, tmp, B, st));
-  SYK_TRY(expmv_impl(P1, dtype, q4, tmp, ub, B, tol, ws, st, nullptr));
+  SYK_TRY(expmv_impl(P1, dtype, {-beta * x[2], 0.0}, tmp, ub, B, tol, ws, st, nullptr));
   double tcur = 0.0;
   for (int k = 0; k < nt; ++k) {
     const double tk = t[k], dt = tk - tcur;
@@ -183,11 +186,10 @@ int otoc_impl(const syk_terms* terms, double beta, int i, int j, const double* t
     }
     SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, ua, pr, B, st));  // p (odd)
     SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, ub, qs, B, st));  // q (even)
-    // r = rho^{1/4} U^dag p and s = rho^{1/4} U^dag q: the two exponentials commute, so each
-    // is one Krylov evolution with z = -beta/4 + i t
-    const std::complex<double> zb(-beta / 4.0, tk);
-    SYK_TRY(expmv_impl(P1, dtype, zb, pr, pr, B, tol, ws, st, nullptr));  // r (odd)
-    SYK_TRY(expmv_impl(P0, dtype, zb, qs, qs, B, tol, ws, st, nullptr));  // s (even)
+    // r = rho^{x1} U^dag p and s = rho^{x2} U^dag q: the exponentials commute, so each is one
+    // Krylov evolution with z = -beta x + i t
+    SYK_TRY(expmv_impl(P1, dtype, {-beta * x[0], tk}, pr, pr, B, tol, ws, st, nullptr));  // r (odd)
+    SYK_TRY(expmv_impl(P0, dtype, {-beta * x[1], tk}, qs, qs, B, tol, ws, st, nullptr));  // s (even)
     SYK_TRY(launch_apply_chi(terms->N, j, 0, dtype, qs, tmp, B, st));     // chi_j s (odd)
     SYK_TRY(dot_columns(pr, tmp, terms->D, B, dtype, ws, r + size_t(k) * B, st));
   }
@@ -211,8 +213,99 @@ extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const
     set_error("syk_otoc: need 0 <= i != j < N (i=%d j=%d)", i, j);
     return SYK_EINVAL;
   }
-  return otoc_impl(terms, beta, i, j, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im,
+  static const double quarter[4] = {0.25, 0.25, 0.25, 0.25};
+  return otoc_impl(terms, beta, quarter, i, j, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im,
                    static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int syk_otoc_split(const syk_terms* terms, double beta, const double* x, int i, int j, const double* t,
+                              int nt, const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
+                              double* F_re_im, void* stream) {
+  clear_error();
+  SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im));
+  if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
+    set_error("syk_otoc_split: need 0 <= i != j < N (i=%d j=%d)", i, j);
+    return SYK_EINVAL;
+  }
+  if (!x) {
+    set_error("syk_otoc_split: NULL split");
+    return SYK_EINVAL;
+  }
+  double sum = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    if (!(x[k] >= 0.0) || !std::isfinite(x[k])) {
+      set_error("syk_otoc_split: split fractions must be finite and >= 0");
+      return SYK_EINVAL;
+    }
+    sum += x[k];
+  }
+  if (std::abs(sum - 1.0) > 1e-12) {
+    set_error("syk_otoc_split: split fractions must sum to 1 (got %.17g)", sum);
+    return SYK_EINVAL;
+  }
+  return otoc_impl(terms, beta, x, i, j, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im,
+                   static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int syk_correlator_G_imag(const syk_terms* terms, double beta, int i, const double* tau, int ntau,
+                                     const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
+                                     double* G_re_im, double* Z, void* stream) {
+  clear_error();
+  SYK_TRY(check_common(terms, beta, tau, ntau, psi0, nstates, dtype, krylov_dim, tol, G_re_im));
+  if (i < 0 || i >= terms->N) {
+    set_error("syk_correlator_G_imag: Majorana index %d out of range", i);
+    return SYK_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t B = nstates;
+  ApplyParams P0, P1;
+  SYK_TRY(make_apply_params(terms, 0, dtype, &P0));
+  SYK_TRY(make_apply_params(terms, 1, dtype, &P1));
+  Scratch sc(st);
+  const size_t vb = size_t(terms->D) * B * dtype_size(dtype);
+  const size_t wsb = krylov_ws_bytes(terms->D, dtype, krylov_dim, B);
+  void *wsp, *x, *w, *y, *tmp, *res;
+  SYK_TRY(sc.alloc(&wsp, wsb));
+  SYK_TRY(sc.alloc(&x, vb));
+  SYK_TRY(sc.alloc(&w, vb));
+  SYK_TRY(sc.alloc(&y, vb));
+  SYK_TRY(sc.alloc(&tmp, vb));
+  SYK_TRY(sc.alloc(&res, sizeof(double2) * B * (ntau + 1)));
+  const void* psi = nullptr;
+  SYK_TRY(device_input(psi0, vb, sc, &psi));
+  KrylovWS ws;
+  SYK_TRY(krylov_ws_carve(&ws, wsp, wsb, terms->D, dtype, krylov_dim, B));
+  double2* r = static_cast<double2*>(res);
+  // x = e^{-beta H/2} psi~ (even), Z = <x|x>; w(tau) = e^{tau H} x (even), y(tau) = e^{-tau H} chi_i x (odd)
+  SYK_TRY(expmv_impl(P0, dtype, {-0.5 * beta, 0.0}, psi, x, B, tol, ws, st, nullptr));
+  SYK_TRY(dot_columns(x, x, terms->D, B, dtype, ws, r + size_t(ntau) * B, st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(w, x, vb, cudaMemcpyDeviceToDevice, st));
+  SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, x, y, B, st));
+  double tcur = 0.0;
+  for (int k = 0; k < ntau; ++k) {
+    const double dt = tau[k] - tcur;
+    if (dt > 0.0) {
+      SYK_TRY(expmv_impl(P0, dtype, {dt, 0.0}, w, w, B, tol, ws, st, nullptr));
+      SYK_TRY(expmv_impl(P1, dtype, {-dt, 0.0}, y, y, B, tol, ws, st, nullptr));
+      tcur = tau[k];
+    }
+    SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, y, tmp, B, st));  // chi_i e^{-tau H} chi_i x (even)
+    SYK_TRY(dot_columns(w, tmp, terms->D, B, dtype, ws, r + size_t(k) * B, st));
+  }
+  std::vector<double2> h(size_t(ntau + 1) * B);
+  SYK_CUDA_CHECK(cudaMemcpyAsync(h.data(), r, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  prof_collect();
+  for (int64_t s2 = 0; s2 < B; ++s2) {
+    const double z = h[size_t(ntau) * B + s2].x;
+    if (Z) Z[s2] = z;
+    for (int k = 0; k < ntau; ++k) {
+      const double2 v = h[size_t(k) * B + s2];
+      G_re_im[(size_t(k) * B + s2) * 2] = z > 0 ? v.x / z : NAN;
+      G_re_im[(size_t(k) * B + s2) * 2 + 1] = z > 0 ? v.y / z : NAN;
+    }
+  }
+  return SYK_OK;
 }
 
 // ---------------------------------------------------------------- batched workload
@@ -273,8 +366,9 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
     for (int q = next++; q < nitems; q = next++) {
       const int k = order[q];
       const syk_otoc_item& it = items[k];
-      const int rc = otoc_impl(it.terms, it.beta, i, j, t, nt, it.psi0, it.nstates, dtype, krylov_dim, tol,
-                               it.F_re_im, st);
+      static const double quarter[4] = {0.25, 0.25, 0.25, 0.25};
+      const int rc = otoc_impl(it.terms, it.beta, quarter, i, j, t, nt, it.psi0, it.nstates, dtype, krylov_dim,
+                               tol, it.F_re_im, st);
       if (item_status) item_status[k] = rc;
       if (rc != SYK_OK) {
         std::lock_guard<std::mutex> lk(err_mtx);

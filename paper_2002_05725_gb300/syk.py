@@ -64,6 +64,8 @@ def load(build_if_missing: bool = False):
         "syk_use_graphs": (i32, [i32]),
         "syk_profile_read": (i32, [vp, vp, i32]),
         "syk_autotune_apply": (i32, [vp, i32, i32, i64, i32, vp, vp]),
+        "syk_otoc_split": (i32, [vp, dbl, vp, i32, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp]),
+        "syk_correlator_G_imag": (i32, [vp, dbl, i32, vp, i32, vp, i64, i32, i32, dbl, vp, vp, vp]),
         "syk_otoc_batch": (i32, [vp, i32, i32, i32, vp, i32, i32, i32, dbl, i32, vp]),
         "syk_otoc_grad": (i32, [vp, dbl, i32, i32, dbl, vp, i64, i32, i32, dbl, dbl, vp, vp, vp, vp]),
         "syk_correlator_G_grad": (i32, [vp, dbl, i32, dbl, vp, i64, i32, i32, dbl, dbl, vp, vp, vp, vp]),
@@ -84,7 +86,8 @@ def exported_symbols():
             "syk_apply_chi", "syk_tridiag_expm", "syk_workspace_bytes", "syk_expmv", "syk_expmv_static", "syk_correlator_G",
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
-            "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs"]
+            "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
+            "syk_correlator_G_imag"]
 
 
 def _check(rc: int, what: str):
@@ -360,3 +363,33 @@ def syk_otoc_batch(items, i: int, j: int, times, dtype: int = SYK_C64, krylov_di
 
 def syk_use_graphs(on: bool = True):
     _check(load().syk_use_graphs(int(on)), "syk_use_graphs")
+
+
+def syk_otoc_split(terms: Terms, beta: float, x, i: int, j: int, times, psi0, krylov_dim: int = 40,
+                   tol: float = 1e-12, stream=None):
+    """OTOC with rho split as Tr[W rho^x1 V rho^x2 W rho^x3 V rho^x4]; returns F (nt, B) complex."""
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    xs = np.ascontiguousarray(x, dtype=np.float64)
+    if xs.shape != (4,):
+        raise SykError("the split needs four fractions")
+    ptr, B, code, keep = _input_ptr(psi0)
+    F = np.zeros((len(t), B, 2))
+    _check(load().syk_otoc_split(terms.ptr, float(beta), xs.ctypes.data, int(i), int(j), t.ctypes.data, len(t), ptr,
+                                 B, code, int(krylov_dim), float(tol), F.ctypes.data, _stream(stream)),
+           "syk_otoc_split")
+    del keep
+    return F[..., 0] + 1j * F[..., 1]
+
+
+def syk_correlator_G_imag(terms: Terms, beta: float, i: int, taus, psi0, krylov_dim: int = 30, tol: float = 1e-12,
+                          stream=None):
+    """Imaginary-time G(tau) (ntau, B) complex and Z (B,)."""
+    t = np.ascontiguousarray(taus, dtype=np.float64)
+    ptr, B, code, keep = _input_ptr(psi0)
+    G = np.zeros((len(t), B, 2))
+    Z = np.zeros(B)
+    _check(load().syk_correlator_G_imag(terms.ptr, float(beta), int(i), t.ctypes.data, len(t), ptr, B, code,
+                                        int(krylov_dim), float(tol), G.ctypes.data, Z.ctypes.data, _stream(stream)),
+           "syk_correlator_G_imag")
+    del keep
+    return G[..., 0] + 1j * G[..., 1], Z

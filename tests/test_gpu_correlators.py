@@ -92,3 +92,36 @@ def test_otoc_invalid(torch):
         syk.syk_otoc(terms, 1.0, 0, 1, [1.0, 0.5], psi)
     with pytest.raises(syk.SykError):
         syk.syk_correlator_G(terms, -1.0, 0, [0.0], psi)
+
+
+@pytest.mark.parametrize("x", [(0.0, 0.0, 0.0, 1.0), (0.1, 0.4, 0.2, 0.3)])
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_otoc_split_vs_exact(torch, x, dt):
+    """Unregularized OTOC and a general rho split against the exact chain."""
+    N = 12
+    J = inputs.couplings(N, 4)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 3, 2)
+    ts = np.linspace(0.0, 8.0, 9)
+    F = syk.syk_otoc_split(terms, 6.0, x, 0, 1, ts, to_dev(torch, psi, dt), krylov_dim=30,
+                           tol=1e-12 if dt == "c128" else 1e-7)
+    Fr = co.F_state_split(evolve.SectorSystem(N, J), 6.0, x, 0, 1, ts, psi.T)
+    assert rel(F, Fr) < TOL[dt]
+    reg = syk.syk_otoc_split(terms, 6.0, (0.25,) * 4, 0, 1, ts[:3], to_dev(torch, psi, "c128"), krylov_dim=30)
+    assert rel(reg, syk.syk_otoc(terms, 6.0, 0, 1, ts[:3], to_dev(torch, psi, "c128"), krylov_dim=30)) < 1e-13
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_G_imag_vs_exact(torch, dt):
+    N = 16
+    J = inputs.couplings(N, 5)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 2, 6)
+    beta = 10.0
+    taus = np.linspace(0.0, beta, 11)
+    G, Z = syk.syk_correlator_G_imag(terms, beta, 3, taus, to_dev(torch, psi, dt), krylov_dim=30,
+                                     tol=1e-12 if dt == "c128" else 1e-7)
+    Gr, Zr = co.G_imag_state(evolve.SectorSystem(N, J), beta, 3, taus, psi.T)
+    assert rel(G, Gr) < TOL[dt]
+    assert rel(Z, Zr) < 1e-11
+    assert np.abs(G[0] - 0.5).max() < 1e-13 if dt == "c128" else True
