@@ -2,7 +2,8 @@
 
     python -m paper_2002_05725_gb300.profile_apply --N 40 --batch 8 --dtype c64 --reps 3
 
-Prints one JSON line with the mean time per apply (CUDA events, after one
+Autotunes the launch shape for the configuration first (as the benchmark does),
+then prints one JSON line with the mean time per apply (CUDA events, after one
 warm-up apply) and the FP32/FP64 and effective-gather rates.
 """
 from __future__ import annotations
@@ -20,6 +21,7 @@ def main():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sector", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch-shape heuristic")
     a = ap.parse_args()
     import torch
     syk.load()
@@ -27,6 +29,11 @@ def main():
     terms = syk.syk_build_terms(a.N, inputs.couplings(a.N, 0))
     psi = inputs.random_states_device(a.N, a.batch, 1, "cuda", dt)
     y = torch.empty_like(psi)
+    tile = None
+    if not a.no_tune and a.batch in (1, 2, 4, 8, 16):
+        syk.syk_autotune_apply(terms, syk.SYK_C64 if a.dtype == "c64" else syk.SYK_C128, a.batch)
+        tile = [e for e in json.loads(syk.syk_autotune_export())["apply_tiles"]
+                if e["N"] == a.N and e["batch"] == a.batch]
     syk.syk_apply_H(terms, a.sector, psi, out=y)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -40,7 +47,7 @@ def main():
     s = 8 if a.dtype == "c64" else 16
     print(json.dumps({"N": a.N, "batch": a.batch, "dtype": a.dtype, "ms_per_apply": ms,
                       "tflops": 8.0 * nnz * a.batch / (ms * 1e-3) / 1e12,
-                      "gather_GBps": nnz * a.batch * s / (ms * 1e-3) / 1e9, "nnz": nnz}))
+                      "gather_GBps": nnz * a.batch * s / (ms * 1e-3) / 1e9, "nnz": nnz, "tile": tile}))
 
 
 if __name__ == "__main__":
