@@ -530,9 +530,10 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     ntb = tc.ntb;  // autotuned
     cs = tc.cs;
   } else {
-    // 256-thread CTAs (narrower only if the sector is smaller than a tile); if the grid
-    // has too few warps, the mask chunks of a tile are split across a cluster of CTAs
-    while (ntb > 6 && p.D < ((int64_t)Cfg::RPT << ntb)) --ntb;
+    // 256-thread CTAs, narrower if the sector is smaller than a tile or a CTA would need more
+    // than ~80 KB of shared memory (fewer than 2 resident CTAs per SM); if the grid has too
+    // few warps, the mask chunks of a tile are split across a cluster of CTAs
+    while (ntb > 6 && (p.D < ((int64_t)Cfg::RPT << ntb) || Cfg::smem(Cfg::RPT << ntb) > 80 * 1024)) --ntb;
     const int64_t nt = p.D / ((int64_t)Cfg::RPT << ntb);
     while (cs < 8 && nt * cs * ((1 << ntb) / 32) < 152 * 32) cs *= 2;
   }

@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sector", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch-shape heuristic")
+    ap.add_argument("--tile", default=None, help="force the launch shape 'ntb,cluster' (no tuning sweep)")
     a = ap.parse_args()
     import torch
     syk.load()
@@ -30,8 +31,14 @@ def main():
     psi = inputs.random_states_device(a.N, a.batch, 1, "cuda", dt)
     y = torch.empty_like(psi)
     tile = None
-    if not a.no_tune and a.batch in (1, 2, 4, 8, 16):
-        syk.syk_autotune_apply(terms, syk.SYK_C64 if a.dtype == "c64" else syk.SYK_C128, a.batch)
+    code = syk.SYK_C64 if a.dtype == "c64" else syk.SYK_C128
+    if a.tile:
+        ntb, cs = (int(v) for v in a.tile.split(","))
+        syk.syk_autotune_import(json.dumps({"apply_tiles": [{"N": a.N, "dtype": code, "batch": a.batch,
+                                                             "ntb": ntb, "cluster": cs}]}))
+        tile = {"ntb": ntb, "cluster": cs, "forced": True}
+    elif not a.no_tune and a.batch in (1, 2, 4, 8, 16):
+        syk.syk_autotune_apply(terms, code, a.batch)
         tile = [e for e in json.loads(syk.syk_autotune_export())["apply_tiles"]
                 if e["N"] == a.N and e["batch"] == a.batch]
     syk.syk_apply_H(terms, a.sector, psi, out=y)
