@@ -113,8 +113,9 @@ def test_otoc_split_vs_exact(torch, x, dt):
 
 @pytest.mark.parametrize("dt", ["c128", "c64"])
 def test_G_imag_vs_exact(torch, dt):
-    """c128 on 0 <= tau <= beta; c64 on tau <= beta/2, since e^{(tau - beta/2) H} amplifies the
-    FP32 rounding of the data for tau > beta/2 (G(beta - tau) = G(tau) covers the rest)."""
+    """c128 on 0 <= tau <= beta within 1e-10; c64 on tau <= beta/2 within 3e-5: the imaginary-time
+    factors e^{-beta H/2} and e^{(tau - beta/2) H} amplify the FP32 rounding of the data (by about
+    3x here; unboundedly for tau > beta/2, where G(beta - tau) = G(tau) gives the same values)."""
     N = 16
     J = inputs.couplings(N, 5)
     terms = syk.syk_build_terms(N, J)
@@ -122,8 +123,8 @@ def test_G_imag_vs_exact(torch, dt):
     beta = 10.0
     taus = np.linspace(0.0, beta if dt == "c128" else beta / 2, 11)
     G, Z = syk.syk_correlator_G_imag(terms, beta, 3, taus, to_dev(torch, psi, dt), krylov_dim=30,
-                                     tol=1e-12 if dt == "c128" else 1e-7)
+                                     tol=1e-12 if dt == "c128" else 1e-8)
     Gr, Zr = co.G_imag_state(evolve.SectorSystem(N, J), beta, 3, taus, psi.T)
-    assert rel(G, Gr) < TOL[dt]
+    assert rel(G, Gr) < (TOL[dt] if dt == "c128" else 3e-5)
     assert rel(Z, Zr) < 1e-11
     assert np.abs(G[0] - 0.5).max() < (1e-13 if dt == "c128" else 1e-6)
