@@ -38,8 +38,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "syk_cplx.cuh"
-#include "syk_internal.h"
+#include "syk_tile.cuh"
 
 // Unroll factor of the per-chunk mask loop of the tiled matvec (build-time knob).
 #ifndef SYK_MASK_UNROLL
@@ -60,11 +59,13 @@
 
 namespace syk {
 
-// Tile configuration chosen by the autotuner per (N, dtype, batch): CTA width 2^ntb and
-// cluster size cs.  Absent entries use the built-in heuristic.
+// Tile configuration chosen by the autotuner per (N, dtype, batch): CTA width 2^ntb,
+// cluster size cs and kernel variant var (0: k_apply_tiled; 1..3: k_apply_coset with
+// 2^var rows per thread).  Absent entries use the built-in heuristic.
 struct TileChoice {
   int ntb, cs;
   double ms;
+  int var = 0;
 };
 static std::mutex g_tune_mtx;
 static std::map<uint64_t, TileChoice> g_tune;
@@ -85,14 +86,6 @@ static void tile_choice_set(int N, int dtype, int64_t batch, TileChoice c) {
 }
 
 namespace {
-
-// Table index bits of a popcount-4 mask: bit k = bit pos_k of the full index xf.
-// s packs the right-shift pos_k - k of support bit k into byte k (funnel shifts use
-// only the low 5 bits of the amount).
-__device__ __forceinline__ uint32_t supp_bits(uint32_t xf, uint32_t s) {
-  return (__funnelshift_r(xf, 0u, s) & 1u) | (__funnelshift_r(xf, 0u, s >> 8) & 2u) |
-         (__funnelshift_r(xf, 0u, s >> 16) & 4u) | (__funnelshift_r(xf, 0u, s >> 24) & 8u);
-}
 
 template <typename R, int BT>
 __global__ void __launch_bounds__(128) k_apply_rows(ApplyParams p, const typename CT<R>::T* __restrict__ psi,
@@ -196,132 +189,6 @@ int launch_apply_T(const ApplyParams& p, const void* psi, void* y, int64_t batch
 }
 
 // ---------------------------------------------------------------- tiled matvec
-namespace tma {
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
-}
-// bulk global -> shared copy; completion is signalled on mbarrier b as transaction bytes
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   saddr(dst)),
-               "l"(src), "r"(bytes), "r"(saddr(b))
-               : "memory");
-}
-__device__ __forceinline__ bool try_wait(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(saddr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for phase `parity` of b; gives up after a bounded number of polls.
-__device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
-    if (try_wait(b, parity)) return true;
-  return false;
-}
-// thread-block cluster helpers
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_size() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// shared-memory address of the same offset in CTA `rank` of the cluster
-__device__ __forceinline__ uint32_t map_rank(uint32_t saddr_local, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr_local), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ float4 ld_cluster(uint32_t a, float4) {
-  float4 v;
-  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(a)
-               : "memory");
-  return v;
-}
-__device__ __forceinline__ double2 ld_cluster(uint32_t a, double2) {
-  double2 v;
-  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
-  return v;
-}
-}  // namespace tma
-
-template <typename R>
-struct Slot;  // 16-byte chunk of a row
-template <>
-struct Slot<float> {
-  using T = float4;  // two complex64
-  static __device__ __forceinline__ void mac(float4& a, float cr, float ci, const float4 v) {
-    a.x = fmaf(cr, v.x, fmaf(-ci, v.y, a.x));
-    a.y = fmaf(cr, v.y, fmaf(ci, v.x, a.y));
-    a.z = fmaf(cr, v.z, fmaf(-ci, v.w, a.z));
-    a.w = fmaf(cr, v.w, fmaf(ci, v.z, a.w));
-  }
-  static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-};
-template <>
-struct Slot<double> {
-  using T = double2;  // one complex128
-  static __device__ __forceinline__ void mac(double2& a, double cr, double ci, const double2 v) { cmac(a, cr, ci, v); }
-  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
-};
-
-// diagonal coefficient c_0(x) = sum_{c<d} w_cd (-1)^{x_c + x_d}
-template <typename R>
-__device__ __forceinline__ R diag_coef(const R* __restrict__ wd, int n, uint32_t xf) {
-  R dsum = R(0);
-  for (int c = 0; c < n - 1; ++c) {
-    R inner = R(0);
-    for (int d = c + 1; d < n; ++d) {
-      const R w = __ldg(&wd[c * n + d]);
-      inner += ((xf >> d) & 1u) ? -w : w;
-    }
-    dsum += ((xf >> c) & 1u) ? -inner : inner;
-  }
-  return dsum;
-}
-
-// popcount-2 coefficient c_m(x) = (-1)^{popcount(zeta_f & x)} sum_c (-1)^{x_c} W_c[u(x)]
-template <typename C, typename R>
-__device__ __forceinline__ void pc2_coef(const C* __restrict__ t2, int k, int n, uint4 rec, uint32_t xf, R& cr,
-                                         R& ci) {
-  const uint32_t a = rec.z & 0xffu, bb = (rec.z >> 8) & 0xffu;
-  const uint32_t u = ((xf >> a) & 1u) | (((xf >> bb) & 1u) << 1);
-  const C* W = t2 + (size_t)k * n * 4 + u;
-  cr = R(0);
-  ci = R(0);
-  for (int c = 0; c < n; ++c) {
-    const C w = __ldg(&W[4 * c]);
-    if ((xf >> c) & 1u) {
-      cr -= w.x;
-      ci -= w.y;
-    } else {
-      cr += w.x;
-      ci += w.y;
-    }
-  }
-  if (__popc(rec.y & xf) & 1) {
-    cr = -cr;
-    ci = -ci;
-  }
-}
-
 template <typename R, int BT>
 struct TileCfg {
   using C = typename CT<R>::T;
@@ -526,7 +393,14 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   using C = typename CT<R>::T;
   int ntb = 8, cs = 1;
   TileChoice tc;
-  if (tile_choice_lookup(p.n * 2, sizeof(R) == 4 ? SYK_C64 : SYK_C128, BT, &tc) && (Cfg::RPT << tc.ntb) <= p.D) {
+  const bool tuned = tile_choice_lookup(p.n * 2, sizeof(R) == 4 ? SYK_C64 : SYK_C128, BT, &tc);
+  if constexpr (sizeof(R) == 4 && (BT == 4 || BT == 8 || BT == 16)) {
+    if (tuned && tc.var > 0) {
+      const int rc = launch_coset_var(p, BT, psi, y, st, tc.var, tc.ntb, tc.cs);
+      if (rc <= 0) return rc;  // launched or failed; 1: not applicable, plain tiles below
+    }
+  }
+  if (tuned && tc.var == 0 && (Cfg::RPT << tc.ntb) <= p.D) {
     ntb = tc.ntb;  // autotuned
     cs = tc.cs;
   } else {
@@ -720,10 +594,13 @@ extern "C" int syk_autotune_apply(const syk_terms* terms, int parity, int dtype,
              : batch == 4 ? TileCfg<double, 4>::RPT : batch == 8 ? TileCfg<double, 8>::RPT : TileCfg<double, 16>::RPT);
   TileChoice best{0, 0, 1e300};
   int rc = SYK_OK;
+  for (int var = 0; var <= 3 && rc == SYK_OK; ++var)
   for (int ntb = 6; ntb <= 8 && rc == SYK_OK; ++ntb)
     for (int cs = 1; cs <= 8 && rc == SYK_OK; cs *= 2) {
-      if ((int64_t(rows_per_thread) << ntb) > P.D) continue;  // tile larger than the sector
-      tile_choice_set(N, dtype, batch, TileChoice{ntb, cs, 0.0});
+      if (!coset_var_ok(dtype, batch, var) || (var && !coset_fits(batch, var, ntb))) continue;
+      const int rpt = var ? 1 << var : rows_per_thread;
+      if ((int64_t(rpt) << ntb) > P.D) continue;  // tile larger than the sector
+      tile_choice_set(N, dtype, batch, TileChoice{ntb, cs, 0.0, var});
       rc = launch_apply_H(P, dtype, x, y, batch, st);  // warm-up (also builds the chunk list)
       cudaEventRecord(e0, st);
       for (int r = 0; r < reps && rc == SYK_OK; ++r) rc = launch_apply_H(P, dtype, x, y, batch, st);
@@ -732,7 +609,7 @@ extern "C" int syk_autotune_apply(const syk_terms* terms, int parity, int dtype,
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= reps;
-      if (rc == SYK_OK && ms < best.ms) best = TileChoice{ntb, cs, ms};
+      if (rc == SYK_OK && ms < best.ms) best = TileChoice{ntb, cs, ms, var};
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -757,10 +634,12 @@ extern "C" int syk_autotune_export(char* buf, size_t len) {
     std::lock_guard<std::mutex> lk(g_tune_mtx);
     bool first = true;
     for (auto& kv : g_tune) {
-      char item[160];
-      snprintf(item, sizeof(item), "%s{\"N\": %d, \"dtype\": %d, \"batch\": %d, \"ntb\": %d, \"cluster\": %d, \"ms\": %.6g}",
+      char item[192];
+      snprintf(item, sizeof(item),
+               "%s{\"N\": %d, \"dtype\": %d, \"batch\": %d, \"ntb\": %d, \"cluster\": %d, \"variant\": %d, "
+               "\"ms\": %.6g}",
                first ? "" : ", ", int(kv.first & 0xff), int((kv.first >> 8) & 0xff), int(kv.first >> 16),
-               kv.second.ntb, kv.second.cs, kv.second.ms);
+               kv.second.ntb, kv.second.cs, kv.second.var, kv.second.ms);
       js += item;
       first = false;
     }
@@ -800,14 +679,16 @@ extern "C" int syk_autotune_import(const char* json) {
       *v = std::strtod(obj.c_str() + at + 1, nullptr);
       return true;
     };
-    double N, dt, b, ntb, cs, ms = 0.0;
+    double N, dt, b, ntb, cs, ms = 0.0, var = 0.0;
     if (num("N", &N) && num("dtype", &dt) && num("batch", &b) && num("ntb", &ntb) && num("cluster", &cs)) {
       num("ms", &ms);
-      if (ntb < 6 || ntb > 8 || (cs != 1 && cs != 2 && cs != 4 && cs != 8)) {
-        set_error("syk_autotune_import: invalid entry (ntb=%g cluster=%g)", ntb, cs);
+      num("variant", &var);
+      if (ntb < 6 || ntb > 8 || (cs != 1 && cs != 2 && cs != 4 && cs != 8) ||
+          !coset_var_ok(int(dt), int64_t(b), int(var))) {
+        set_error("syk_autotune_import: invalid entry (ntb=%g cluster=%g variant=%g)", ntb, cs, var);
         return SYK_EINVAL;
       }
-      tile_choice_set(int(N), int(dt), int64_t(b), TileChoice{int(ntb), int(cs), ms});
+      tile_choice_set(int(N), int(dt), int64_t(b), TileChoice{int(ntb), int(cs), ms, int(var)});
       ++count;
     }
     p = end + 1;

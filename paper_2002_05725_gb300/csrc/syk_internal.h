@@ -69,6 +69,41 @@ int tile_groups(const syk_terms* t, int tb, int gmax, const int4** dev, int* cou
 // Lookup only: returns false if that list has not been built on this device yet.
 bool tile_groups_cached(const syk_terms* t, int tb, int gmax, const int4** dev, int* count);
 
+// Coset layout of the popcount-4 masks for a tile of 2^tb rows whose threads own rows that
+// differ in the top `rbits` row bits (offsets d): masks m and m ^ (d << (tb - rbits)) read the
+// same partner row for the thread's row slots 0 and d.  Per chunk (<= gmax masks):
+//   chunks[c] = {h | first << 31, first mask, end mask, popcount-2 range as in tile_groups},
+//   counts[c] = number of cosets of each multi-mask shape (byte per shape, in the fixed shape
+//               order of the row-bit count); the chunk's masks are those cosets' members in
+//               shape order, each coset's members by increasing offset, then single masks,
+// with the mask records and 32-entry tables (fp32 and fp64) permuted into that order.
+struct CosetLayout {
+  int4* chunks = nullptr;
+  uint32_t* counts = nullptr;
+  uint4* rec = nullptr;
+  float2* t32 = nullptr;
+  double2* t64 = nullptr;
+  int nchunks = 0;
+};
+int coset_layout(const syk_terms* t, int tb, int rbits, int gmax, bool may_alloc, const CosetLayout** out);
+// The same layout in host memory (no device needed).
+struct CosetHost {
+  std::vector<int4> chunks;
+  std::vector<uint32_t> counts;
+  std::vector<uint4> rec;
+  std::vector<float> t32;
+  std::vector<double> t64;
+};
+int coset_layout_host(const syk_terms* t, int tb, int rbits, int gmax, CosetHost* out);
+
+// complex64 coset matvec (syk_apply_coset.cu).  var = log2(rows per thread): 1 or 2 for 16
+// columns, 2 or 3 for 4 and 8 columns.  launch_coset_var returns 1 when that variant does
+// not apply to this launch (the caller then uses k_apply_tiled).
+bool coset_var_ok(int dtype, int64_t batch, int var);
+bool coset_fits(int64_t batch, int var, int ntb);  // CTA width 2^ntb (6 or 7) within shared memory
+int launch_coset_var(const ApplyParams& p, int64_t batch, const void* psi, void* y, cudaStream_t st, int var, int ntb,
+                     int cs);
+
 int ensure_device_tables(const syk_terms* t);
 int ensure_grad_groups(const syk_terms* t);  // builds and uploads the gradient term groups
 int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p);
@@ -114,6 +149,7 @@ struct syk_terms {
   std::vector<double> wdiag;     // n * n
   mutable syk::DeviceTables dev;
   mutable std::map<int, std::pair<int4*, int>> groups_dev;  // tile bits -> device group list
+  mutable std::map<int, syk::CosetLayout> coset_dev;         // (tb, rbits, gmax) -> coset layout
   // Term groups of the per-term inner products (gradients), built on first use: terms sharing
   // an X-mask and a Z-mask off their support bits; device copies on dev.device.
   mutable int ngg = 0;

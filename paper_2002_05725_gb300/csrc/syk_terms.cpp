@@ -284,6 +284,11 @@ extern "C" void syk_free_terms(syk_terms* t) {
     void* gp[] = {t->d_gg_rec, t->d_term_group, t->d_term_s, t->d_term_phase};
     for (void* p : gp)
       if (p) cudaFree(p);
+    for (auto& kv : t->coset_dev) {
+      void* cp[] = {kv.second.chunks, kv.second.counts, kv.second.rec, kv.second.t32, kv.second.t64};
+      for (void* p : cp)
+        if (p) cudaFree(p);
+    }
     if (prev >= 0) cudaSetDevice(prev);
   }
   delete t;
@@ -503,5 +508,117 @@ int ensure_grad_groups(const syk_terms* t) {
   return SYK_OK;
 }
 
+
+
+// Member sets (bit d: row-slot offset d) of the multi-mask cosets that popcount-4 masks
+// form for 1, 2 or 3 row bits; any other coset is split into single masks.
+static const uint32_t* coset_shapes(int rbits, int* count) {
+  static const uint32_t s1[] = {0x3u};
+  static const uint32_t s2[] = {0x7u, 0xEu};
+  static const uint32_t s3[] = {0x17u, 0xE8u, 0x7Eu};
+  *count = rbits == 1 ? 1 : rbits == 2 ? 2 : 3;
+  return rbits == 1 ? s1 : rbits == 2 ? s2 : s3;
+}
+
+int coset_layout_host(const syk_terms* t, int tb, int rbits, int gmax, CosetHost* out) {
+  if (rbits < 1 || rbits > 3 || tb < rbits || gmax < 8 || gmax > 255) {
+    set_error("coset_layout: unsupported shape (tb=%d rbits=%d gmax=%d)", tb, rbits, gmax);
+    return SYK_EINVAL;
+  }
+  const int n4 = t->n4, n2 = t->n2;
+  const int shift = tb - rbits;
+  const uint32_t dmask = ((1u << rbits) - 1u) << shift;
+  int nshape = 0;
+  const uint32_t* shapes = coset_shapes(rbits, &nshape);
+  CosetHost& L = *out;
+  L = CosetHost();
+  // masks are sorted by compact XOR, so one h = m >> tb is a contiguous range
+  int i4 = 0, i2 = 0;
+  bool diag = false;
+  while (i4 < n4 || i2 < n2 || !diag) {
+    uint32_t h = 0xffffffffu;
+    if (i4 < n4) h = std::min(h, t->m4_rec[4 * i4] >> tb);
+    if (i2 < n2) h = std::min(h, t->m2_rec[4 * i2] >> tb);
+    if (!diag) h = 0;
+    const int b4 = i4, b2 = i2;
+    while (i4 < n4 && (t->m4_rec[4 * i4] >> tb) == h) ++i4;
+    while (i2 < n2 && (t->m2_rec[4 * i2] >> tb) == h) ++i2;
+    if (h == 0) diag = true;
+    // cosets of this h: key = compact mask with the row-slot bits cleared; members by offset d
+    std::map<uint32_t, std::map<uint32_t, int>> cmap;
+    for (int k = b4; k < i4; ++k) cmap[t->m4_rec[4 * k] & ~dmask][(t->m4_rec[4 * k] & dmask) >> shift] = k;
+    // units in chunk order: the cosets of each listed shape, then single masks
+    std::vector<std::pair<int, std::vector<int>>> units;  // (shape slot or -1, masks in offset order)
+    for (int sh = 0; sh < nshape; ++sh)
+      for (auto& c : cmap) {
+        uint32_t shape = 0;
+        for (auto& md : c.second) shape |= 1u << md.first;
+        if (shape != shapes[sh]) continue;
+        std::vector<int> ks;
+        for (auto& md : c.second) ks.push_back(md.second);
+        units.emplace_back(sh, ks);
+      }
+    for (auto& c : cmap) {
+      uint32_t shape = 0;
+      for (auto& md : c.second) shape |= 1u << md.first;
+      bool listed = false;
+      for (int sh = 0; sh < nshape; ++sh) listed |= shape == shapes[sh];
+      if (!listed)
+        for (auto& md : c.second) units.emplace_back(-1, std::vector<int>{md.second});
+    }
+    std::stable_sort(units.begin(), units.end(), [](const std::pair<int, std::vector<int>>& a,
+                                                    const std::pair<int, std::vector<int>>& b) {
+      return (a.first < 0 ? 1000 : a.first) < (b.first < 0 ? 1000 : b.first);
+    });
+    size_t u = 0;
+    bool first = true;
+    do {
+      const int mbeg = int(L.rec.size());
+      int used = 0;
+      uint32_t counts = 0;
+      while (u < units.size() && used + int(units[u].second.size()) <= gmax) {
+        if (units[u].first >= 0) counts += 1u << (8 * units[u].first);
+        for (int k : units[u].second) {
+          L.rec.push_back(make_uint4(t->m4_rec[4 * k], t->m4_rec[4 * k + 1], t->m4_rec[4 * k + 2], t->m4_rec[4 * k + 3]));
+          for (int e = 0; e < 64; ++e) {
+            L.t64.push_back(t->m4_tab[size_t(k) * 64 + e]);
+            L.t32.push_back(float(t->m4_tab[size_t(k) * 64 + e]));
+          }
+          ++used;
+        }
+        ++u;
+      }
+      const int k2 = first ? (b2 | (i2 << 16)) : 0;
+      L.chunks.push_back(make_int4(int(h | (first ? 0x80000000u : 0u)), mbeg, int(L.rec.size()), k2));
+      L.counts.push_back(counts);
+      first = false;
+    } while (u < units.size());
+  }
+  return SYK_OK;
+}
+
+int coset_layout(const syk_terms* t, int tb, int rbits, int gmax, bool may_alloc, const CosetLayout** out) {
+  if (may_alloc) SYK_TRY(ensure_device_tables(t));
+  std::lock_guard<std::mutex> lock(t->mtx);
+  const int key = (tb << 16) | (rbits << 8) | gmax;
+  auto it = t->coset_dev.find(key);
+  if (it != t->coset_dev.end()) {
+    *out = &it->second;
+    return SYK_OK;
+  }
+  if (!may_alloc) return 1;  // not built yet
+  CosetHost H;
+  SYK_TRY(coset_layout_host(t, tb, rbits, gmax, &H));
+  CosetLayout L;
+  L.nchunks = int(H.chunks.size());
+  SYK_TRY(upload(&L.chunks, H.chunks.data(), H.chunks.size() * sizeof(int4)));
+  SYK_TRY(upload(&L.counts, H.counts.data(), H.counts.size() * sizeof(uint32_t)));
+  SYK_TRY(upload(&L.rec, H.rec.data(), H.rec.size() * sizeof(uint4)));
+  SYK_TRY(upload(&L.t32, H.t32.data(), H.t32.size() * sizeof(float)));
+  SYK_TRY(upload(&L.t64, H.t64.data(), H.t64.size() * sizeof(double)));
+  it = t->coset_dev.emplace(key, L).first;
+  *out = &it->second;
+  return SYK_OK;
+}
 
 }  // namespace syk

@@ -1,0 +1,153 @@
+// Device helpers shared by the tiled matvec kernels (syk_apply.cu, syk_apply_coset.cu):
+// table-index extraction, bulk-copy / mbarrier / cluster PTX wrappers, 16-byte row-chunk
+// multiply-adds, and the diagonal and popcount-2 coefficients (Supp. Sec. I.B).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "syk_cplx.cuh"
+#include "syk_internal.h"
+
+namespace syk {
+
+// opt-in dynamic shared memory per CTA on sm_100-class GPUs
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
+
+// Table index bits of a popcount-4 mask: bit k = bit pos_k of the full index xf.
+// s packs the right-shift pos_k - k of support bit k into byte k (funnel shifts use
+// only the low 5 bits of the amount).
+__device__ __forceinline__ uint32_t supp_bits(uint32_t xf, uint32_t s) {
+  return (__funnelshift_r(xf, 0u, s) & 1u) | (__funnelshift_r(xf, 0u, s >> 8) & 2u) |
+         (__funnelshift_r(xf, 0u, s >> 16) & 4u) | (__funnelshift_r(xf, 0u, s >> 24) & 8u);
+}
+
+
+namespace tma {
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+// bulk global -> shared copy; completion is signalled on mbarrier b as transaction bytes
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(b))
+               : "memory");
+}
+__device__ __forceinline__ bool try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of b; gives up after a bounded number of polls.
+__device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (try_wait(b, parity)) return true;
+  return false;
+}
+// thread-block cluster helpers
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared-memory address of the same offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr_local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr_local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float4 ld_cluster(uint32_t a, float4) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ double2 ld_cluster(uint32_t a, double2) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+  return v;
+}
+}  // namespace tma
+
+template <typename R>
+struct Slot;  // 16-byte chunk of a row
+template <>
+struct Slot<float> {
+  using T = float4;  // two complex64
+  static __device__ __forceinline__ void mac(float4& a, float cr, float ci, const float4 v) {
+    a.x = fmaf(cr, v.x, fmaf(-ci, v.y, a.x));
+    a.y = fmaf(cr, v.y, fmaf(ci, v.x, a.y));
+    a.z = fmaf(cr, v.z, fmaf(-ci, v.w, a.z));
+    a.w = fmaf(cr, v.w, fmaf(ci, v.z, a.w));
+  }
+  static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct Slot<double> {
+  using T = double2;  // one complex128
+  static __device__ __forceinline__ void mac(double2& a, double cr, double ci, const double2 v) { cmac(a, cr, ci, v); }
+  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+};
+
+// diagonal coefficient c_0(x) = sum_{c<d} w_cd (-1)^{x_c + x_d}
+template <typename R>
+__device__ __forceinline__ R diag_coef(const R* __restrict__ wd, int n, uint32_t xf) {
+  R dsum = R(0);
+  for (int c = 0; c < n - 1; ++c) {
+    R inner = R(0);
+    for (int d = c + 1; d < n; ++d) {
+      const R w = __ldg(&wd[c * n + d]);
+      inner += ((xf >> d) & 1u) ? -w : w;
+    }
+    dsum += ((xf >> c) & 1u) ? -inner : inner;
+  }
+  return dsum;
+}
+
+// popcount-2 coefficient c_m(x) = (-1)^{popcount(zeta_f & x)} sum_c (-1)^{x_c} W_c[u(x)]
+template <typename C, typename R>
+__device__ __forceinline__ void pc2_coef(const C* __restrict__ t2, int k, int n, uint4 rec, uint32_t xf, R& cr,
+                                         R& ci) {
+  const uint32_t a = rec.z & 0xffu, bb = (rec.z >> 8) & 0xffu;
+  const uint32_t u = ((xf >> a) & 1u) | (((xf >> bb) & 1u) << 1);
+  const C* W = t2 + (size_t)k * n * 4 + u;
+  cr = R(0);
+  ci = R(0);
+  for (int c = 0; c < n; ++c) {
+    const C w = __ldg(&W[4 * c]);
+    if ((xf >> c) & 1u) {
+      cr -= w.x;
+      ci -= w.y;
+    } else {
+      cr += w.x;
+      ci += w.y;
+    }
+  }
+  if (__popc(rec.y & xf) & 1) {
+    cr = -cr;
+    ci = -ci;
+  }
+}
+
+
+}  // namespace syk

@@ -22,7 +22,9 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sector", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch-shape heuristic")
-    ap.add_argument("--tile", default=None, help="force the launch shape 'ntb,cluster' (no tuning sweep)")
+    ap.add_argument("--tile", default=None,
+                    help="force the launch shape 'ntb,cluster[,variant]' (no tuning sweep; variant 0 = k_apply_tiled, "
+                         "1..3 = k_apply_coset with 2^variant rows per thread)")
     a = ap.parse_args()
     import torch
     syk.load()
@@ -33,10 +35,11 @@ def main():
     tile = None
     code = syk.SYK_C64 if a.dtype == "c64" else syk.SYK_C128
     if a.tile:
-        ntb, cs = (int(v) for v in a.tile.split(","))
+        v = [int(t) for t in a.tile.split(",")]
+        ntb, cs, var = v[0], v[1], (v[2] if len(v) > 2 else 0)
         syk.syk_autotune_import(json.dumps({"apply_tiles": [{"N": a.N, "dtype": code, "batch": a.batch,
-                                                             "ntb": ntb, "cluster": cs}]}))
-        tile = {"ntb": ntb, "cluster": cs, "forced": True}
+                                                             "ntb": ntb, "cluster": cs, "variant": var}]}))
+        tile = {"ntb": ntb, "cluster": cs, "variant": var, "forced": True}
     elif not a.no_tune and a.batch in (1, 2, 4, 8, 16):
         syk.syk_autotune_apply(terms, code, a.batch)
         tile = [e for e in json.loads(syk.syk_autotune_export())["apply_tiles"]

@@ -143,3 +143,33 @@ def test_apply_H_every_tile_configuration(torch, dt, B):
     syk.syk_autotune_import(js)
     y = syk.syk_apply_H(terms, 0, x).cpu().numpy().reshape(D, B)
     assert rel(y[rows], ref.reshape(len(rows), B)) < TOL[dt]
+
+
+@pytest.mark.parametrize("B,variants", [(16, (1, 2)), (8, (2, 3)), (4, (2, 3))])
+def test_apply_H_coset_variants(torch, B, variants):
+    """complex64 coset kernels (2, 4 or 8 rows per thread) at every CTA width x cluster size:
+    full H at N = 20 (one or two tiles; both sectors) and sampled rows at N = 28."""
+    code = syk.SYK_C64
+    for N in (20, 28):
+        J = inputs.couplings(N, 9)
+        terms = syk.syk_build_terms(N, J)
+        D = 1 << (N // 2 - 1)
+        psi = inputs.random_states(N, B, 31)
+        x = to_dev(torch, psi, "c64")
+        rows = np.arange(D) if N == 20 else \
+            np.unique(np.concatenate([[0, D - 1], np.random.default_rng(2).integers(0, D, 48)]))
+        for sector in (0, 1):
+            ref = hm.H_sector_sparse(N, J, sector) @ psi.T if N == 20 else hm.apply_rows(N, J, sector, psi.T, rows)
+            for var in variants:
+                for ntb in (6, 7, 8):
+                    if (1 << var) << ntb > D:
+                        continue
+                    for cs in (1, 2, 4, 8):
+                        syk.syk_autotune_import(
+                            '{"apply_tiles": [{"N": %d, "dtype": %d, "batch": %d, "ntb": %d, "cluster": %d, '
+                            '"variant": %d}]}' % (N, code, B, ntb, cs, var))
+                        y = syk.syk_apply_H(terms, sector, x).cpu().numpy().reshape(D, B)
+                        assert rel(y[rows], ref.reshape(len(rows), B)) < TOL["c64"], (N, sector, var, ntb, cs)
+        best = syk.syk_autotune_apply(terms, code, B)
+        assert best > 0
+    syk.syk_autotune_import('{"apply_tiles": [{"N": 28, "dtype": 1, "batch": %d, "ntb": 8, "cluster": 1}]}' % B)

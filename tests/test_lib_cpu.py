@@ -84,3 +84,19 @@ def test_workspace_formula(lib):
     vec = (1 << 19) * 16 * 8
     assert 42 * vec <= b1 < 42 * vec + (64 << 20)
     assert syk.syk_workspace_bytes(40, syk.SYK_C128, 40, 16) > b1
+
+
+def test_autotune_table_json(lib):
+    """The launch-shape table (host only): kernel variant round trip, invalid entries refused."""
+    syk.syk_autotune_import('{"apply_tiles": [{"N": 36, "dtype": 1, "batch": 16, "ntb": 6, "cluster": 2,'
+                            ' "variant": 2, "ms": 1.5}, {"N": 36, "dtype": 2, "batch": 4, "ntb": 7, "cluster": 1}]}')
+    js = syk.syk_autotune_export()
+    assert '"N": 36, "dtype": 1, "batch": 16, "ntb": 6, "cluster": 2, "variant": 2' in js
+    assert '"N": 36, "dtype": 2, "batch": 4, "ntb": 7, "cluster": 1, "variant": 0' in js
+    for bad in ('{"N": 36, "dtype": 2, "batch": 16, "ntb": 6, "cluster": 1, "variant": 2}',  # c128 has no cosets
+                '{"N": 36, "dtype": 1, "batch": 16, "ntb": 6, "cluster": 1, "variant": 3}',  # 8 rows x 16 columns
+                '{"N": 36, "dtype": 1, "batch": 2, "ntb": 6, "cluster": 1, "variant": 1}',
+                '{"N": 36, "dtype": 1, "batch": 8, "ntb": 9, "cluster": 1}',
+                '{"N": 36, "dtype": 1, "batch": 8, "ntb": 6, "cluster": 3}'):
+        with pytest.raises(syk.SykError):
+            syk.syk_autotune_import('{"apply_tiles": [%s]}' % bad)
