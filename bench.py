@@ -71,12 +71,22 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def ncu_traffic(N, states, dtype):
+def matvec_kernel(tile, states, dtype):
+    """Name and source file of the matvec kernel a tuned launch shape selects."""
+    if tile and tile.get("variant", 0) > 0:
+        return (f"k_apply_coset<{states}, RB={tile['variant']}, ntb={tile['ntb']}> (cluster {tile['cluster']})",
+                "coset", "syk_apply_coset.cu")
+    R = "float" if dtype == "c64" else "double"
+    shape = f" (ntb={tile['ntb']}, cluster {tile['cluster']})" if tile else ""
+    return f"k_apply_tiled<{R}, {states}>" + shape, "tiled", "syk_apply.cu"
+
+
+def ncu_traffic(N, states, dtype, kind="tiled", source="syk_apply.cu"):
     """DRAM bytes per matvec launch from the committed ncu summary of this configuration,
     or None if there is none or the kernel source changed since it was captured."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"apply_tiled_N{N}_B{states}_{dtype}.md")
-    src = os.path.join(ROOT, "paper_2002_05725_gb300", "csrc", "syk_apply.cu")
+    path = os.path.join(ROOT, "profiles", f"apply_{kind}_N{N}_B{states}_{dtype}.md")
+    src = os.path.join(ROOT, "paper_2002_05725_gb300", "csrc", source)
     try:
         text = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -356,7 +366,9 @@ def gpu_main(a, rank, world, local_rank):
     if a.dtype == "c128":
         peak = peak / 64.0  # FP64 FMA rate of GB300 is 1/64 of FP32
     achieved = flops / (avg_ms * 1e-3) / 1e12
-    traffic, traffic_src = ncu_traffic(a.N, a.states, a.dtype)
+    tile = next((e for e in tuned if e["N"] == a.N and e["batch"] == a.states and e["dtype"] == code), None)
+    kname, kind, ksrc = matvec_kernel(tile, a.states, a.dtype)
+    traffic, traffic_src = ncu_traffic(a.N, a.states, a.dtype, kind, ksrc)
     esz = 8 if a.dtype == "c64" else 16
     gather = nnz * a.states * esz / (avg_ms * 1e-3) / 1e9
     line = {
@@ -364,14 +376,14 @@ def gpu_main(a, rank, world, local_rank):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
         "config": config_dict(a, times),
-        "roofline": {"kernel": "apply_H (k_apply_tiled)", "bound": bound, "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
                                   + (" / 64 (FP64)" if a.dtype == "c128" else ""),
                      "per_launch": {"flops": flops, "avg_ms": avg_ms, "launches": prof["launches"]}},
         "hpsi": {"gather_GBps": gather, "hbm_peak_GBps": pk.get("hbm_gbs"), "gather_frac_of_hbm":
                  gather / float(pk.get("hbm_gbs", 6800.0)), "peak_kind": pk_kind},
-        "apply_tile": next((e for e in tuned if e["N"] == a.N and e["batch"] == a.states), None),
+        "apply_tile": tile,
         "applies_per_curve": applies_per_state,
         "applies_per_curve_model": applies_model(a.N, a.beta, times[1:], a.krylov, a.tol),
         "krylov_bases_per_step": cnt["krylov_bases"] / max(1, a.steps),
