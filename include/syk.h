@@ -246,10 +246,15 @@ int syk_correlator_G_grad(const syk_terms* terms, double beta, int i, double t, 
 int syk_autotune_apply(const syk_terms* terms, int parity, int dtype, int64_t batch, int reps,
                        void* stream, double* best_ms);
 /* syk_autotune_export / _import -- the tuned table as JSON
- * ({"apply_tiles": [{"N":..,"dtype":..,"batch":..,"ntb":..,"cluster":..,"ms":..}]}),
+ * ({"apply_tiles": [{"N":..,"dtype":..,"batch":..,"ntb":..,"cluster":..,"variant":..,"ms":..}]};
+ * variant 0 is the plain tiled kernel, 1..3 the complex64 coset kernel with 2^variant rows
+ * per thread; a missing variant reads as 0),
  * so a tuning run can be cached in a file and reloaded. */
 int syk_autotune_export(char* buf, size_t len);
 int syk_autotune_import(const char* json);
+/* syk_autotune_reset -- forgets every tuned entry, so later launches use the built-in
+ * launch-shape heuristic again.  Host only; returns 0. */
+int syk_autotune_reset(void);
 
 /* ------------------------------------------------------------- diagnostics
  * syk_last_error -- message of the last failed call on this thread ("" if none). */

@@ -398,6 +398,19 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     if (tuned && tc.var > 0) {
       const int rc = launch_coset_var(p, BT, psi, y, st, tc.var, tc.ntb, tc.cs);
       if (rc <= 0) return rc;  // launched or failed; 1: not applicable, plain tiles below
+    } else if (!tuned) {
+      // untuned default: the coset kernel (faster than the plain one at every N = 28..40 and
+      // 4/8/16 columns measured), one row bit for 16 columns and two for 4 and 8, 128-thread
+      // CTAs from sector 2^18 up, cluster split while the grid has fewer than 32 warps per SM
+      const int var = BT == 16 ? 1 : 2;
+      const int vntb = p.D >= (int64_t(1) << 18) ? 7 : 6;
+      if ((int64_t(1) << (var + vntb)) <= p.D) {
+        const int64_t nt = p.D >> (var + vntb);
+        int vcs = 1;
+        while (vcs < 8 && nt * vcs * ((1 << vntb) / 32) < 152 * 32) vcs *= 2;
+        const int rc = launch_coset_var(p, BT, psi, y, st, var, vntb, vcs);
+        if (rc <= 0) return rc;
+      }
     }
   }
   if (tuned && tc.var == 0 && (Cfg::RPT << tc.ntb) <= p.D) {
@@ -650,6 +663,16 @@ extern "C" int syk_autotune_export(char* buf, size_t len) {
     return SYK_EINVAL;
   }
   std::memcpy(buf, js.c_str(), js.size() + 1);
+  return SYK_OK;
+}
+
+extern "C" int syk_autotune_reset(void) {
+  using namespace syk;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mtx);
+    g_tune.clear();
+  }
+  bump_graph_epoch();  // captured matvec launches carry the old tile shapes
   return SYK_OK;
 }
 

@@ -71,6 +71,7 @@ def load(build_if_missing: bool = False):
         "syk_correlator_G_grad": (i32, [vp, dbl, i32, dbl, vp, i64, i32, i32, dbl, dbl, vp, vp, vp, vp]),
         "syk_autotune_export": (i32, [ctypes.c_char_p, sz]),
         "syk_autotune_import": (i32, [ctypes.c_char_p]),
+        "syk_autotune_reset": (i32, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -87,7 +88,7 @@ def exported_symbols():
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
-            "syk_correlator_G_imag"]
+            "syk_correlator_G_imag", "syk_autotune_reset"]
 
 
 def _check(rc: int, what: str):
@@ -299,6 +300,11 @@ def syk_autotune_export() -> str:
 
 def syk_autotune_import(text: str):
     _check(load().syk_autotune_import(text.encode()), "syk_autotune_import")
+
+
+def syk_autotune_reset():
+    """Forgets every tuned launch shape (the built-in heuristic applies again)."""
+    _check(load().syk_autotune_reset(), "syk_autotune_reset")
 
 
 def syk_otoc_grad(terms: Terms, beta: float, i: int, j: int, t: float, psi0, krylov_dim: int = 40,

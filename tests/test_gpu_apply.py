@@ -173,3 +173,29 @@ def test_apply_H_coset_variants(torch, B, variants):
         best = syk.syk_autotune_apply(terms, code, B)
         assert best > 0
     syk.syk_autotune_import('{"apply_tiles": [{"N": 28, "dtype": 1, "batch": %d, "ntb": 8, "cluster": 1}]}' % B)
+
+
+def test_apply_H_bench_size_launch_shapes(torch):
+    """The benchmark's matvec at full size (N = 40, sector 2^19, 16 states, complex64) in the
+    launch shapes it runs: the untuned default, the coset shapes the autotuner picks on GB300
+    (2 rows per thread, 128-thread CTAs, cluster 1 and 2), the 4-row coset shape and the plain
+    tiled kernel; sampled rows (first, last, random) against the oracle's term-by-term sum."""
+    N, B = 40, 16
+    J = inputs.couplings(N, 0)
+    terms = syk.syk_build_terms(N, J)
+    D = 1 << (N // 2 - 1)
+    psi = inputs.random_states(N, B, 0)
+    x = to_dev(torch, psi, "c64")
+    rows = np.unique(np.concatenate([[0, 1, D - 1], np.random.default_rng(40).integers(0, D, 21)]))
+    shapes = [None, (7, 1, 1), (7, 2, 1), (6, 1, 2), (6, 1, 0)]
+    for sector in (0, 1):
+        ref = hm.apply_rows(N, J, sector, psi.T, rows)
+        for sh in shapes:
+            syk.syk_autotune_reset()  # None: the built-in default shape
+            if sh is not None:
+                ntb, cs, var = sh
+                syk.syk_autotune_import('{"apply_tiles": [{"N": 40, "dtype": 1, "batch": 16, "ntb": %d, '
+                                        '"cluster": %d, "variant": %d}]}' % (ntb, cs, var))
+            y = syk.syk_apply_H(terms, sector, x).cpu().numpy().reshape(D, B)
+            assert rel(y[rows], ref.reshape(len(rows), B)) < TOL["c64"], (sector, sh)
+    syk.syk_autotune_reset()

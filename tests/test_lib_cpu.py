@@ -100,3 +100,5 @@ def test_autotune_table_json(lib):
                 '{"N": 36, "dtype": 1, "batch": 8, "ntb": 6, "cluster": 3}'):
         with pytest.raises(syk.SykError):
             syk.syk_autotune_import('{"apply_tiles": [%s]}' % bad)
+    syk.syk_autotune_reset()
+    assert syk.syk_autotune_export() == '{"apply_tiles": []}'
