@@ -93,13 +93,16 @@ def ncu_traffic(N, states, dtype, kind="tiled", source="syk_apply.cu"):
     except OSError:
         return None, None
     vals = {}
+    keys = ("traffic_bytes_per_launch", "kernel_source_sha256", "smem_wavefronts_per_launch",
+            "tma_fill_bytes_per_launch")
     for line in text.splitlines():
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256")):
+        if ":" in line and line.strip().startswith(keys):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha256") != sha or "traffic_bytes_per_launch" not in vals:
         return None, os.path.relpath(path, ROOT)
-    return float(vals["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
+    out = {k: float(v) for k, v in vals.items() if k != "kernel_source_sha256"}
+    return out, os.path.relpath(path, ROOT)
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -368,7 +371,17 @@ def gpu_main(a, rank, world, local_rank):
     achieved = flops / (avg_ms * 1e-3) / 1e12
     tile = next((e for e in tuned if e["N"] == a.N and e["batch"] == a.states and e["dtype"] == code), None)
     kname, kind, ksrc = matvec_kernel(tile, a.states, a.dtype)
-    traffic, traffic_src = ncu_traffic(a.N, a.states, a.dtype, kind, ksrc)
+    ncu_vals, traffic_src = ncu_traffic(a.N, a.states, a.dtype, kind, ksrc)
+    traffic = ncu_vals["traffic_bytes_per_launch"] if ncu_vals else None
+    smem = None
+    if ncu_vals and "smem_wavefronts_per_launch" in ncu_vals:
+        # the matvec's binding unit: the SMs' shared-memory port (128 B per cycle per SM)
+        sbytes = ncu_vals["smem_wavefronts_per_launch"] * 128 + ncu_vals.get("tma_fill_bytes_per_launch", 0.0)
+        speak = N_SM * 128 * sm_mhz * 1e6 / 1e9
+        sach = sbytes / (avg_ms * 1e-3) / 1e9
+        smem = {"achieved": sach, "peak": speak, "unit": "GB/s", "frac": sach / speak, "bytes": sbytes,
+                "source": "ncu LSU shared-memory wavefronts x 128 B + bulk-copy fill bytes, per launch",
+                "peak_kind": f"derived: {N_SM} SMs x 128 B/cycle x {sm_mhz:.0f} MHz"}
     esz = 8 if a.dtype == "c64" else 16
     gather = nnz * a.states * esz / (avg_ms * 1e-3) / 1e9
     line = {
@@ -380,7 +393,8 @@ def gpu_main(a, rank, world, local_rank):
                      "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
                                   + (" / 64 (FP64)" if a.dtype == "c128" else ""),
-                     "per_launch": {"flops": flops, "avg_ms": avg_ms, "launches": prof["launches"]}},
+                     "per_launch": {"flops": flops, "avg_ms": avg_ms, "launches": prof["launches"]},
+                     "shared_memory": smem},
         "hpsi": {"gather_GBps": gather, "hbm_peak_GBps": pk.get("hbm_gbs"), "gather_frac_of_hbm":
                  gather / float(pk.get("hbm_gbs", 6800.0)), "peak_kind": pk_kind},
         "apply_tile": tile,

@@ -129,3 +129,18 @@ def test_G_imag_vs_exact(torch, dt):
     tol = {"c128": (TOL["c128"], 1e-11, 1e-13), "c64": (3e-5, 1e-5, 2e-5)}[dt]
     errs = (rel(G, Gr), rel(Z, Zr), np.abs(G[0] - 0.5).max())
     assert all(e < t for e, t in zip(errs, tol)), (errs, tol)
+
+
+def test_otoc_N40_bench_parameters_c64_vs_c128(torch):
+    """The benchmark's workload parameters at full size (N = 40, sector 2^19, beta J = 10,
+    Krylov dimension 40, W = chi_0, V = chi_1): complex64 vectors with FP64 scalars against the
+    complex128 path, two states, t = 0 and the first grid point 1.2; F~(0) = 1 exactly."""
+    N = 40
+    J = inputs.couplings(N, 0)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 2, 0)
+    ts = [0.0, 1.2]
+    a = syk.syk_otoc(terms, 10.0, 0, 1, ts, to_dev(torch, psi, "c128"), krylov_dim=40, tol=1e-12)
+    b = syk.syk_otoc(terms, 10.0, 0, 1, ts, to_dev(torch, psi, "c64"), krylov_dim=40, tol=1e-7)
+    assert rel(b / b[0], a / a[0]) < TOL["c64"]
+    assert np.allclose(b[0] / b[0], 1.0)
