@@ -234,6 +234,26 @@ int syk_correlator_G_grad(const syk_terms* terms, double beta, int i, double t, 
                           int64_t nstates, int dtype, int krylov_dim, double tol, double quad_dz,
                           double* G_re_im, double* dG_dJ, double* dG_dbeta, void* stream);
 
+/* syk_lowest_eigenvalues -- the k lowest eigenvalues of H in sector `parity`, for the
+ * finite-size rescaling (Supp. Sec. "Finite-size rescaling method": only sizes whose lowest
+ * 20 eigenstates lie within the thermal window of the ground state enter the extrapolation).
+ * Lanczos from the start vector psi0 (D complex amplitudes of `dtype`, device or host
+ * memory; a random state reaches every eigenvector with probability 1) with full two-pass
+ * Gram-Schmidt reorthogonalisation, up to max_steps (<= SYK_MAX_EIG_STEPS) steps; every 16
+ * steps the Ritz values of the tridiagonal projection are computed on the host (FP64) and
+ * the run stops once the k lowest have residual bounds beta_j |y_i(j)| <= tol * max(1, |T|)
+ * (|T|: the largest Ritz value in magnitude, at least 1).  Outputs (host): evals[k], the k
+ * lowest DISTINCT levels ascending (Ritz values closer than 10 tol |T| are one level: SYK
+ * levels are doubly degenerate within a sector for N = 4 mod 8, and rounding lets a single
+ * start vector find both members of a pair), resid[k] (may be NULL) their residual bounds,
+ * *nsteps (may be NULL) the Lanczos steps taken.  Returns SYK_ENUMERIC if the k levels have
+ * not converged within max_steps (outputs filled as far as known) or the Krylov space of
+ * psi0 holds fewer than k levels; synchronises `stream`.
+ * Device scratch: (min(max_steps, D) + 2) vectors. */
+#define SYK_MAX_EIG_STEPS 4096
+int syk_lowest_eigenvalues(const syk_terms* terms, int parity, int dtype, const void* psi0, int k, int max_steps,
+                           double tol, double* evals, double* resid, int* nsteps, void* stream);
+
 /* ------------------------------------------------------------- autotuner
  * syk_autotune_apply -- times every tile configuration of the tiled matvec
  * (CTA width 64/128/256 threads x thread-block cluster of 1/2/4/8 CTAs sharing a

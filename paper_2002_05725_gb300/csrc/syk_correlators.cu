@@ -19,26 +19,6 @@
 namespace syk {
 namespace {
 
-// Device buffers owned by one correlator call.
-struct Scratch {
-  cudaStream_t st;
-  std::vector<void*> ptrs;
-  explicit Scratch(cudaStream_t s) : st(s) {}
-  ~Scratch() {
-    for (void* p : ptrs) cudaFreeAsync(p, st);
-  }
-  int alloc(void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, bytes, st);
-    if (e != cudaSuccess) {
-      set_error("cannot allocate %zu bytes of device memory: %s", bytes, cudaGetErrorString(e));
-      *p = nullptr;
-      return SYK_ENOMEM;
-    }
-    ptrs.push_back(*p);
-    return SYK_OK;
-  }
-};
-
 int check_common(const syk_terms* t, double beta, const double* times, int nt, const void* psi0, int64_t ns,
                  int dtype, int kd, double tol, const void* out) {
   if (!t || !times || !psi0 || !out) {
@@ -61,22 +41,6 @@ int check_common(const syk_terms* t, double beta, const double* times, int nt, c
     }
     prev = times[k];
   }
-  return SYK_OK;
-}
-
-// Returns a device copy of psi0 if it is host memory, else psi0 itself.
-int device_input(const void* psi0, size_t bytes, Scratch& sc, const void** out) {
-  cudaPointerAttributes at;
-  cudaError_t e = cudaPointerGetAttributes(&at, psi0);
-  if (e != cudaSuccess) cudaGetLastError();
-  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
-    *out = psi0;
-    return SYK_OK;
-  }
-  void* d = nullptr;
-  SYK_TRY(sc.alloc(&d, bytes));
-  SYK_CUDA_CHECK(cudaMemcpyAsync(d, psi0, bytes, cudaMemcpyHostToDevice, sc.st));
-  *out = d;
   return SYK_OK;
 }
 

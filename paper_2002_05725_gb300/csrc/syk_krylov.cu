@@ -714,6 +714,53 @@ int expmv_impl(const ApplyParams& P, int dtype, std::complex<double> z, const vo
                           : expmv_T<double>(P, dtype, z, psi, out, tol, ws, st, nsteps);
 }
 
+namespace {
+template <typename R>
+int lanczos_steps_T(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st) {
+  const size_t vs = size_t(ws.D) * ws.B;
+  const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
+  for (int j = j0; j < j1; ++j) {
+    SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, ws.B, st));
+    // two passes of classical Gram-Schmidt against the whole basis for both vector types:
+    // Ritz values of a long run need the basis orthogonal to working precision
+    Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
+    reduce_parts(ws, j + 1, ws.h1, st);
+    Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, nullptr, st);
+    Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
+    reduce_parts(ws, j + 1, ws.h2, st);
+    Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
+    k_lanczos_scalars<<<1, 128, 0, st>>>(j, int(ws.B), ws.G, ws.h1, ws.h2, ws.npart, ws.alpha, ws.beta, ws.inv,
+                                         ws.status, bt);
+    count_launch();
+    if (j + 1 < ws.m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
+  }
+  SYK_CUDA_CHECK(cudaGetLastError());
+  return SYK_OK;
+}
+}  // namespace
+
+int lanczos_begin(int dtype, const void* psi, KrylovWS& ws, cudaStream_t st) {
+  SYK_CUDA_CHECK(cudaMemsetAsync(ws.status, 0, sizeof(int) * 4, st));
+  if (dtype == SYK_C64) Ops<float>::dots(ws, 1, psi, 0, psi, st);
+  else Ops<double>::dots(ws, 1, psi, 0, psi, st);
+  reduce_parts(ws, 1, ws.h1, st);
+  k_norm_init<<<(int(ws.B) + 127) / 128, 128, 0, st>>>(int(ws.B), ws.h1, ws.beta0, ws.inv, ws.status);
+  count_launch();
+  if (dtype == SYK_C64) Ops<float>::scale(ws, psi, ws.vec(0), ws.inv, st);
+  else Ops<double>::scale(ws, psi, ws.vec(0), ws.inv, st);
+  SYK_CUDA_CHECK(cudaGetLastError());
+  return SYK_OK;
+}
+
+int lanczos_steps(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st) {
+  if (j0 < 0 || j1 > ws.m || j0 > j1) {
+    set_error("lanczos_steps: steps [%d, %d) outside the workspace's %d", j0, j1, ws.m);
+    return SYK_EINVAL;
+  }
+  return dtype == SYK_C64 ? lanczos_steps_T<float>(P, dtype, ws, j0, j1, st)
+                          : lanczos_steps_T<double>(P, dtype, ws, j0, j1, st);
+}
+
 }  // namespace syk
 
 // ---------------------------------------------------------------- C ABI

@@ -1,6 +1,7 @@
 // Krylov workspace and internal entry points shared by expmv and the correlators.
 #pragma once
 #include <complex>
+#include <vector>
 
 #include "syk_internal.h"
 
@@ -47,5 +48,49 @@ int dot_columns(const void* x, const void* y, int64_t D, int64_t B, int dtype, K
 
 // Host helpers: pinned staging buffer for small device->host reads.
 void* pinned_scratch(size_t bytes);
+
+// Lanczos for eigenvalues (syk_lowest_eigenvalues): lanczos_begin stores v_0 = psi/||psi||
+// (one column, B = 1); lanczos_steps runs steps [j0, j1) of the three-term recurrence with
+// full two-pass classical Gram-Schmidt reorthogonalisation, writing alpha_j, beta_j to the
+// workspace (ws.alpha, ws.beta; beta_j = 0 marks a breakdown) and v_{j+1} for j + 1 < ws.m.
+int lanczos_begin(int dtype, const void* psi, KrylovWS& ws, cudaStream_t st);
+int lanczos_steps(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st);
+
+// Device buffers owned by one library call (freed, stream-ordered, when it returns).
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  int alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+      set_error("cannot allocate %zu bytes of device memory: %s", bytes, cudaGetErrorString(e));
+      *p = nullptr;
+      return SYK_ENOMEM;
+    }
+    ptrs.push_back(*p);
+    return SYK_OK;
+  }
+};
+
+// Returns a device copy of psi0 if it is host memory, else psi0 itself.
+inline int device_input(const void* psi0, size_t bytes, Scratch& sc, const void** out) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, psi0);
+  if (e != cudaSuccess) cudaGetLastError();
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+    *out = psi0;
+    return SYK_OK;
+  }
+  void* d = nullptr;
+  SYK_TRY(sc.alloc(&d, bytes));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(d, psi0, bytes, cudaMemcpyHostToDevice, sc.st));
+  *out = d;
+  return SYK_OK;
+}
+
 
 }  // namespace syk

@@ -108,6 +108,35 @@ def extrapolate(Ns, lam, degree: int):
     return float(coef[0]), float(math.sqrt(max(cov[0, 0], 0.0))), coef
 
 
+def full_space_levels(N: int, sector_levels: dict, k: int) -> np.ndarray:
+    """The k lowest eigenvalues of H on the whole 2^{N/2}-dimensional space, with multiplicity,
+    from the distinct levels of the parity sectors (sector_levels[0], sector_levels[1]; what
+    single-vector Lanczos returns).  The particle-hole symmetry of the SYK model fixes the
+    degeneracies by N mod 8: for N = 4 mod 8 every level is doubly degenerate within its sector
+    (both sectors needed); for N = 2, 6 mod 8 the two sectors carry the same levels (either one
+    suffices); for N = 0 mod 8 levels are non-degenerate and both sectors are needed."""
+    r = N % 8
+    if r in (2, 6):
+        lv = np.asarray(sector_levels[0] if 0 in sector_levels else sector_levels[1], dtype=np.float64)
+        out = np.repeat(np.sort(lv), 2)
+    else:
+        if 0 not in sector_levels or 1 not in sector_levels:
+            raise ValueError(f"N = {N}: both parity sectors are needed")
+        both = np.concatenate([np.asarray(sector_levels[0], np.float64), np.asarray(sector_levels[1], np.float64)])
+        out = np.sort(np.repeat(both, 2) if r == 4 else both)
+    if len(out) < k:
+        raise ValueError(f"N = {N}: {len(out)} levels known, {k} needed")
+    return out[:k]
+
+
+def sector_levels_needed(N: int, k: int = 20):
+    """(sectors, distinct levels per sector) that `full_space_levels` needs for k full-space levels."""
+    r = N % 8
+    if r in (2, 6):
+        return (0,), (k + 1) // 2
+    return ((0, 1), (k + 1) // 2) if r == 4 else ((0, 1), k)
+
+
 def admissible(evals_by_N: dict, beta: float, k: int = 20, window=None):
     """Sizes whose k lowest eigenvalues lie within `window` (default 1/beta) of the ground state."""
     w = (1.0 / beta) if window is None else float(window)
@@ -156,6 +185,9 @@ def main():
     ap.add_argument("--krylov", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--spectral-window", action="store_true",
+                    help="extrapolate over the sizes whose lowest 20 eigenstates (GPU Lanczos on the first "
+                         "coupling draw) lie within 1/beta of the ground state")
     a = ap.parse_args()
     syk.load()
     Ns = [int(v) for v in a.N.split(",")]
@@ -173,7 +205,29 @@ def main():
     Fs = syk.syk_otoc_batch(items, 0, 1, t, syk.SYK_C64, a.krylov, a.tol, a.workers)
     wall = time.perf_counter() - t0
     Ft = {N: disorder_average([F for F, k in zip(Fs, keys) if k == N]) for N in Ns}
-    res = lyapunov(Ns, t, Ft, a.beta, F0=a.F0)
+    use, low, resid, eig_s = None, {}, {}, 0.0
+    if a.spectral_window:
+        t1 = time.perf_counter()
+        for N in Ns:
+            terms = syk.syk_build_terms(N, inputs.couplings(N, seed=0, realization=0))
+            start = np.ascontiguousarray(inputs.random_states(N, 1, 7)[0].astype(np.complex64))
+            secs, kk = sector_levels_needed(N)
+            lv = {}
+            for sec in secs:
+                # an unconverged run still bounds every level from above (Cauchy interlacing), so
+                # its E_20 - E_0 overestimates the spread; the residuals are reported
+                ev, rs, _ = syk.syk_lowest_eigenvalues(terms, kk, start, parity=sec, max_steps=2048, tol=1e-4,
+                                                       check=False)
+                lv[sec] = ev
+                resid[N] = max(resid.get(N, 0.0), float(np.max(rs)))
+            low[N] = full_space_levels(N, lv, 20)
+        use = admissible(low, a.beta)
+        eig_s = time.perf_counter() - t1
+    res = lyapunov(Ns, t, Ft, a.beta, F0=a.F0, use_Ns=use)
+    if a.spectral_window:
+        res.update({"spectral_window": 1.0 / a.beta, "admissible_N": use, "eig_seconds": eig_s,
+                    "E20_minus_E0": {str(N): float(low[N][19] - low[N][0]) for N in Ns},
+                    "eig_max_residual": {str(N): resid[N] for N in Ns}})
     res.update({"states": a.states, "draws": a.draws, "t_grid": [float(t[0]), float(t[-1]), a.dt],
                 "otoc_seconds": wall, "curves": len(items) * a.states, "dtype": "c64"})
     print(json.dumps(res))

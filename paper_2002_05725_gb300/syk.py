@@ -72,6 +72,7 @@ def load(build_if_missing: bool = False):
         "syk_autotune_export": (i32, [ctypes.c_char_p, sz]),
         "syk_autotune_import": (i32, [ctypes.c_char_p]),
         "syk_autotune_reset": (i32, []),
+        "syk_lowest_eigenvalues": (i32, [vp, i32, i32, vp, i32, i32, dbl, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -88,7 +89,7 @@ def exported_symbols():
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
-            "syk_correlator_G_imag", "syk_autotune_reset"]
+            "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues"]
 
 
 def _check(rc: int, what: str):
@@ -365,6 +366,26 @@ def syk_otoc_batch(items, i: int, j: int, times, dtype: int = SYK_C64, krylov_di
                                  status.ctypes.data), "syk_otoc_batch")
     del keep
     return [F[..., 0] + 1j * F[..., 1] for F in outs]
+
+
+def syk_lowest_eigenvalues(terms: Terms, k: int, psi0, parity: int = 0, max_steps: int = 1024, tol: float = 1e-8,
+                           stream=None, check: bool = True):
+    """k lowest eigenvalues of H in one sector by Lanczos from psi0 (a (D,) or (D, 1) vector).
+
+    Returns (evals (k,), residual bounds (k,), Lanczos steps). With check=False a run that did
+    not converge returns its current Ritz values instead of raising."""
+    ptr, B, code, keep = _input_ptr(psi0)
+    if B != 1:
+        raise SykError("syk_lowest_eigenvalues takes one start vector")
+    ev = np.zeros(int(k))
+    rs = np.zeros(int(k))
+    n = ctypes.c_int(0)
+    rc = load().syk_lowest_eigenvalues(terms.ptr, int(parity), code, ptr, int(k), int(max_steps), float(tol),
+                                       ev.ctypes.data, rs.ctypes.data, ctypes.byref(n), _stream(stream))
+    if check or rc != SYK_ENUMERIC:
+        _check(rc, "syk_lowest_eigenvalues")
+    del keep
+    return ev, rs, n.value
 
 
 def syk_use_graphs(on: bool = True):

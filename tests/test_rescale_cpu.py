@@ -81,3 +81,24 @@ def test_admissible_window():
     # 20th eigenvalue: 3.0 * 19/24, 0.5 * 19/24, 0.1 * 19/24; N=50 has fewer than 20 eigenvalues
     assert rescale.admissible(ev, beta=2.0) == [30, 40]
     assert rescale.admissible(ev, beta=2.0, window=0.1) == [40]
+
+
+@pytest.mark.parametrize("N", [12, 14, 16, 18])
+def test_full_space_levels_match_dense_spectrum(N):
+    """The N mod 8 degeneracy rules (12: doubling within a sector; 14, 18: sectors are copies;
+    16: none) rebuild the lowest full-space levels from distinct sector levels: checked against
+    the oracle's dense full-space spectrum."""
+    from oracle import hamiltonian as hm
+    from paper_2002_05725_gb300 import inputs
+    J = inputs.couplings(N, 2)
+    full = np.linalg.eigvalsh(hm.H_dense(N, J))
+    distinct = {}
+    for sec in (0, 1):
+        ev = np.linalg.eigvalsh(hm.H_sector_sparse(N, J, sec).toarray())
+        keep = np.concatenate([[True], np.diff(ev) > 1e-9])
+        distinct[sec] = ev[keep]
+    secs, kk = rescale.sector_levels_needed(N, 20)
+    got = rescale.full_space_levels(N, {s: distinct[s][:kk] for s in secs}, 20)
+    assert np.allclose(got, full[:20], atol=1e-10)
+    if N % 8 in (2, 6):  # either sector alone suffices
+        assert np.allclose(rescale.full_space_levels(N, {1: distinct[1]}, 20), full[:20], atol=1e-10)
