@@ -15,6 +15,7 @@ import numpy as np
 from . import build as _build
 
 SYK_OK = 0
+SYK_EINVAL, SYK_ENOMEM, SYK_ECUDA, SYK_ENUMERIC, SYK_ETIMEOUT = -1, -2, -3, -4, -5  # include/syk.h
 SYK_C64 = 1
 SYK_C128 = 2
 MAX_KRYLOV = 64

@@ -64,3 +64,17 @@ def test_lowest_eigenvalues_invalid(torch):
         syk.syk_lowest_eigenvalues(terms, 2, np.zeros(8, dtype=np.complex128))  # zero start: no Krylov space
     ev, res, n = syk.syk_lowest_eigenvalues(terms, 8, start)  # the whole sector: all 8 levels exact
     assert np.allclose(ev, np.linalg.eigvalsh(hm.H_sector_sparse(8, J, 0).toarray()), atol=1e-12)
+
+
+def test_lowest_eigenvalues_unconverged_bounds(torch):
+    """A run cut short raises by default; with check=False it returns Ritz values, each an upper
+    bound on the corresponding true level (Cauchy interlacing), with residual bounds above tol."""
+    N = 20
+    J = inputs.couplings(N, 6)
+    terms = syk.syk_build_terms(N, J)
+    start = inputs.random_states(N, 1, 9)[0]
+    with pytest.raises(syk.SykError):
+        syk.syk_lowest_eigenvalues(terms, 6, start, max_steps=16, tol=1e-12)
+    ev, res, n = syk.syk_lowest_eigenvalues(terms, 6, start, max_steps=16, tol=1e-12, check=False)
+    ref = _distinct(np.linalg.eigvalsh(hm.H_sector_sparse(N, J, 0).toarray()))[:6]
+    assert n == 16 and np.all(ev >= ref - 1e-12) and res.max() > 1e-12

@@ -102,3 +102,11 @@ def test_autotune_table_json(lib):
             syk.syk_autotune_import('{"apply_tiles": [%s]}' % bad)
     syk.syk_autotune_reset()
     assert syk.syk_autotune_export() == '{"apply_tiles": []}'
+
+
+def test_return_codes_match_header(lib):
+    """The binding's return-code constants are the header's."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "syk.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (SYK_E[A-Z]+) \((-?\d+)\)", hdr)}
+    assert codes and all(getattr(syk, k) == v for k, v in codes.items())
