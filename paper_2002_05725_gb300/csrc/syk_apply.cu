@@ -54,6 +54,10 @@
 #ifndef SYK_RPT_C64_B16
 #define SYK_RPT_C64_B16 2
 #endif
+// One table lookup per mask for one-state rows when the row-slot bits miss the support.
+#ifndef SYK_SHARED_COEF
+#define SYK_SHARED_COEF 1
+#endif
 #define SYK_PRAGMA(x) _Pragma(#x)
 #define SYK_UNROLL(n) SYK_PRAGMA(unroll n)
 
@@ -306,6 +310,28 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
         const uint32_t idx0 = supp_bits(xf[0], rec.z) | ((__popc(rec.y & xf[0]) & 1u) << 4);
         const uint32_t fl = rec.w >> fsh;
         const C* tab = stab + kk * 32;
+        if constexpr (CH == 0 && SYK_SHARED_COEF) {
+          // one-state rows (8 bytes): the table lookup costs as much shared-memory traffic as
+          // the row itself.  When no row-slot bit of this thread touches the mask's support
+          // (flip bits 0..3 of every row bit clear; the same for the whole warp), every row
+          // slot uses the same table entry up to the sign (flip bit 4), so look it up once.
+          constexpr uint32_t used = RPT >= 8 ? 0x7fffu : RPT >= 4 ? 0x3ffu : RPT >= 2 ? 0x1fu : 0u;
+          if ((fl & used & 0x3def) == 0u) {  // 0x3def: bits 0..3 of each 5-bit flip group
+            const C cf = tab[idx0];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+              uint32_t sg = 0u;
+              if (i & 1) sg ^= fl << 27;
+              if (i & 2) sg ^= fl << 22;
+              if (i & 4) sg ^= fl << 17;
+              sg &= 0x80000000u;  // flip bit 4 of the row bits' groups, moved to the sign bit
+              const R cr = __int_as_float(__float_as_int(cf.x) ^ (int)sg);
+              const R ci = __int_as_float(__float_as_int(cf.y) ^ (int)sg);
+              mac_row(acc[i], cr, ci, tb, (uint32_t)(tid + i * NT) ^ lo);
+            }
+            continue;
+          }
+        }
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           uint32_t idx = idx0;
