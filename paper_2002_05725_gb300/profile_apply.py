@@ -1,4 +1,5 @@
-"""Times syk_apply_H on one configuration (for profilers and quick measurements).
+"""Times syk_apply_H on one configuration (for profilers and quick measurements), and with
+--expmv one real-time evolution step through syk_expmv.
 
     python -m paper_2002_05725_gb300.profile_apply --N 40 --batch 8 --dtype c64 --reps 3
 
@@ -22,6 +23,11 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sector", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch-shape heuristic")
+    ap.add_argument("--expmv", type=float, default=None, metavar="T",
+                    help="also time one real-time step e^{-iHT} psi (Krylov dimension --krylov, tol --tol) and "
+                         "check that it preserves the norm")
+    ap.add_argument("--krylov", type=int, default=20)
+    ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--tile", default=None,
                     help="force the launch shape 'ntb,cluster[,variant]' (no tuning sweep; variant 0 = k_apply_tiled, "
                          "1..3 = k_apply_coset with 2^variant rows per thread)")
@@ -55,9 +61,25 @@ def main():
     ms = e0.elapsed_time(e1) / a.reps
     nnz = terms.D * terms.nmasks
     s = 8 if a.dtype == "c64" else 16
-    print(json.dumps({"N": a.N, "batch": a.batch, "dtype": a.dtype, "ms_per_apply": ms,
-                      "tflops": 8.0 * nnz * a.batch / (ms * 1e-3) / 1e12,
-                      "gather_GBps": nnz * a.batch * s / (ms * 1e-3) / 1e9, "nnz": nnz, "tile": tile}))
+    out = {"N": a.N, "batch": a.batch, "dtype": a.dtype, "ms_per_apply": ms,
+           "tflops": 8.0 * nnz * a.batch / (ms * 1e-3) / 1e12,
+           "gather_GBps": nnz * a.batch * s / (ms * 1e-3) / 1e9, "nnz": nnz, "tile": tile}
+    if a.expmv is not None:
+        # one output step of the real-time evolution, workspace allocated by the call
+        syk.syk_counters(reset=True)
+        e0.record()
+        phi, nb = syk.syk_expmv(terms, a.sector, complex(0.0, -a.expmv), psi, krylov_dim=a.krylov, tol=a.tol,
+                                out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        cnt = syk.syk_counters(reset=True)
+        n0 = torch.linalg.vector_norm(psi.to(torch.complex128), dim=0)
+        n1 = torch.linalg.vector_norm(phi.to(torch.complex128), dim=0)
+        out["expmv"] = {"t": a.expmv, "krylov_dim": a.krylov, "tol": a.tol, "seconds": e0.elapsed_time(e1) / 1e3,
+                        "krylov_bases": nb, "h_applies": cnt["h_applies"] // a.batch,
+                        "workspace_bytes": syk.syk_workspace_bytes(a.N, code, a.krylov, a.batch),
+                        "max_norm_change": float(((n1 - n0).abs() / n0).max())}
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
