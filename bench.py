@@ -56,6 +56,9 @@ def parse():
                     help="mixed-N batched workload (N 20..40, beta J 1/3/10, 8 states per draw)")
     ap.add_argument("--draws", type=int, default=1, help="coupling draws per (N, beta) in --batched mode")
     ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--grad", action="store_true",
+                    help="gradient workload: dF~(t*)/dJ for all couplings and dF~/dbeta at N=28, beta J=5, "
+                         "t*=5, about 200 quadrature sub-intervals, 8 states, c64 and c128")
     return ap.parse_args()
 
 
@@ -460,6 +463,51 @@ def batched_main(a, rank, world, local_rank):
             flush=True)
 
 
+def grad_main(a, rank, world, local_rank):
+    """Gradient workload: F~(t*) and its derivatives w.r.t. all C(N,4) couplings and beta by the
+    adjoint chain (syk_otoc_grad), timed per call after a warm-up call, in c64 and c128."""
+    import torch
+
+    from paper_2002_05725_gb300 import inputs, syk
+    torch.cuda.set_device(local_rank)
+    syk.load()
+    N, beta, tstar, states = 28, 5.0, 5.0, 8
+    quad_dz = 0.05  # |z| rho_est per Gauss-Legendre sub-interval: about 180 sub-intervals for t* = 5
+    terms = syk.syk_build_terms(N, inputs.couplings(N, seed=0, realization=rank))
+    psi = inputs.random_states(N, states, seed=0, realization=rank)
+    res = {}
+    for dt in ("c64", "c128"):
+        x = torch.from_numpy(np.ascontiguousarray(psi.T)).to(
+            torch.complex64 if dt == "c64" else torch.complex128).cuda()
+        tol = 1e-7 if dt == "c64" else 1e-12
+        syk.syk_otoc_grad(terms, beta, 0, 1, tstar, x, krylov_dim=40, tol=tol, quad_dz=quad_dz)  # warm-up
+        syk.syk_counters(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F, dJ, db = syk.syk_otoc_grad(terms, beta, 0, 1, tstar, x, krylov_dim=40, tol=tol, quad_dz=quad_dz)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        cnt = syk.syk_counters(reset=True)
+        res[dt] = {"seconds": wall, "F": F, "dJ": dJ, "db": db, "h_applies": cnt["h_applies"] // states,
+                   "launches": cnt["launches"]}
+    ref = res["c128"]
+    rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+    if rank == 0:
+        print(json.dumps({
+            "metric": "gradient evaluations/hour at N=28 (all couplings and beta, one state each)",
+            "value": world * states * 3600.0 / res["c64"]["seconds"], "unit": "gradients/hour", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": res["c64"]["seconds"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"dF~(t*)/dJ_ijkl (C(28,4) = {inputs.n_terms(N)}) and dF~/dbeta, N=28, "
+                                   f"beta J={beta:g}, t*={tstar:g}, Gauss-Legendre sub-intervals of |z| rho_est <= {quad_dz:g}, "
+                                   f"{states} states, Krylov 40", "N": N},
+            "c128": {"seconds": ref["seconds"], "gradients_per_hour": states * 3600.0 / ref["seconds"],
+                     "h_applies_per_state": ref["h_applies"]},
+            "c64_h_applies_per_state": res["c64"]["h_applies"],
+            "c64_vs_c128": {"F": rel(res["c64"]["F"], ref["F"]), "dJ": rel(res["c64"]["dJ"], ref["dJ"]),
+                            "dbeta": rel(res["c64"]["db"], ref["db"])}}), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -472,6 +520,9 @@ def main():
         return
     if a.batched:
         batched_main(a, rank, world, local_rank)
+        return
+    if a.grad:
+        grad_main(a, rank, world, local_rank)
         return
     if world > 1:
         import torch
