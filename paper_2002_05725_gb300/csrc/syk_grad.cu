@@ -218,6 +218,10 @@ struct GradEngine {
   int expmv(int sector, std::complex<double> z, const void* in, void* out) {
     return expmv_impl(P[sector], dtype, z, in, out, B, tol, ws, st, nullptr);
   }
+  // outs[k] = e^{fr[k] z H} in from the Krylov bases of one evolution (no matvecs per output)
+  int expmv_points(int sector, std::complex<double> z, const void* in, const double* fr, int nf, void* const* outs) {
+    return syk::expmv_points(P[sector], dtype, z, in, fr, nf, outs, B, tol, ws, st);
+  }
   int copy(void* dst, const void* src) {
     SYK_CUDA_CHECK(cudaMemcpyAsync(dst, src, vb, cudaMemcpyDeviceToDevice, st));
     return SYK_OK;
@@ -279,45 +283,41 @@ struct GradEngine {
     const int c = std::max(1, int(std::ceil(std::sqrt(double(S)))));
     const int nseg = (S + c - 1) / c;
     const std::complex<double> zs = z / double(S), zbar = std::conj(z);
-    std::vector<void*> ckpt(nseg), segbuf(c), node(4);
+    std::vector<void*> ckpt(nseg), segbuf(c), node(4), lamq(4);
     for (auto& p : ckpt) SYK_TRY(get(&p));
     for (auto& p : segbuf) SYK_TRY(get(&p));
     for (auto& p : node) SYK_TRY(get(&p));
+    for (auto& p : lamq) SYK_TRY(get(&p));
+    // node fractions of a sub-interval, ascending, for the forward state (from its start) and
+    // for the adjoint (from its end: nodes 3..0, then the start of the sub-interval)
+    double ffwd[4], fadj[5];
+    for (int q = 0; q < 4; ++q) ffwd[q] = 0.5 * (1.0 + kGLx[q]);
+    for (int q = 0; q < 4; ++q) fadj[q] = 1.0 - ffwd[3 - q];
+    fadj[4] = 1.0;
     // forward sweep: checkpoints psi(s/S) for s = 0, c, 2c, ...
     SYK_TRY(copy(ckpt[0], x));
     for (int sg = 1; sg < nseg; ++sg) {
       SYK_TRY(copy(ckpt[sg], ckpt[sg - 1]));
-      for (int s = 0; s < c; ++s) SYK_TRY(expmv(sector, zs, ckpt[sg], ckpt[sg]));
+      SYK_TRY(expmv(sector, zs * double(c), ckpt[sg], ckpt[sg]));  // c sub-intervals in one evolution
     }
     // backward: lam(v) marches from v = 1 to 0
-    double vcur = 1.0;
     for (int sg = nseg - 1; sg >= 0; --sg) {
       const int s0 = sg * c, s1 = std::min(S, s0 + c);
       SYK_TRY(copy(segbuf[0], ckpt[sg]));
       for (int s = s0 + 1; s < s1; ++s) SYK_TRY(expmv(sector, zs, segbuf[s - s0 - 1], segbuf[s - s0]));
       for (int s = s1 - 1; s >= s0; --s) {
-        // forward states at the 4 nodes of [s/S, (s+1)/S], ascending
-        double vq[4];
-        for (int q = 0; q < 4; ++q) vq[q] = (s + 0.5 * (1.0 + kGLx[q])) / S;
-        double vprev = double(s) / S;
-        const void* from = segbuf[s - s0];
-        for (int q = 0; q < 4; ++q) {
-          SYK_TRY(expmv(sector, z * (vq[q] - vprev), from, node[q]));
-          from = node[q];
-          vprev = vq[q];
-        }
-        for (int q = 3; q >= 0; --q) {
-          SYK_TRY(expmv(sector, zbar * (vcur - vq[q]), lam, lam));
-          vcur = vq[q];
-          SYK_TRY(term_grad(sector, lam, node[q], z * (0.5 * kGLw[q] / S), gJ));
-        }
-        SYK_TRY(expmv(sector, zbar * (vcur - double(s) / S), lam, lam));
-        vcur = double(s) / S;
+        // forward states at the 4 nodes of [s/S, (s+1)/S] from one evolution of segbuf[s]
+        SYK_TRY(expmv_points(sector, zs, segbuf[s - s0], ffwd, 4, node.data()));
+        // adjoint at the nodes (3 down to 0) and at s/S from one evolution of lam((s+1)/S)
+        void* aouts[5] = {lamq[3], lamq[2], lamq[1], lamq[0], lam};
+        SYK_TRY(expmv_points(sector, zbar / double(S), lam, fadj, 5, aouts));
+        for (int q = 3; q >= 0; --q) SYK_TRY(term_grad(sector, lamq[q], node[q], z * (0.5 * kGLw[q] / S), gJ));
       }
     }
     for (auto p : ckpt) put(p);
     for (auto p : segbuf) put(p);
     for (auto p : node) put(p);
+    for (auto p : lamq) put(p);
     return SYK_OK;
   }
 

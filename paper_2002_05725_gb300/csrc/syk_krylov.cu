@@ -581,9 +581,12 @@ int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int
   return SYK_OK;
 }
 
+// outs[k] = e^{fr[k] z H} psi for 0 < fr[0] < ... < fr[nf-1]: the step to fr[nf-1] is split
+// into Krylov bases as the error estimate allows, and each output is combined from the basis
+// whose step covers its fraction.  Restarts pass through outs[nf-1], written last.
 template <typename R>
-int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, void* out, double tol,
-            KrylovWS& ws, cudaStream_t st, int* nsteps) {
+int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, const double* fr, int nf,
+            void* const* outs, double tol, KrylovWS& ws, cudaStream_t st, int* nsteps) {
   const int64_t B = ws.B;
   const size_t vs = size_t(ws.D) * B;
   const int m = ws.m;
@@ -599,8 +602,8 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
   int* hstat = static_cast<int*>(ws.host_stage ? ws.host_stage : pinned_scratch(64));
   double* hs = reinterpret_cast<double*>(hstat + 4);
   SYK_CUDA_CHECK(cudaMemsetAsync(ws.status, 0, sizeof(int) * 4, st));
-  double s_rem = 1.0;
-  int steps = 0;
+  double s_rem = fr[nf - 1], s_done = 0.0;
+  int steps = 0, next = 0;
   const void* cur = psi;
   while (s_rem > 0.0) {
     if (++steps > 100000) {
@@ -679,13 +682,30 @@ int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void*
       set_error("expmv: Krylov step collapsed (s=%g of remaining %g); raise krylov_dim or tol", s_acc, s_rem);
       return SYK_ENUMERIC;
     }
-    k_tridiag_coef<<<int(B), 64, 0, st>>>(m_eff, int(B), ws.theta, ws.Q, ws.beta0, zr, zi, nullptr, s_acc, ws.c);
-    count_launch();
-    Ops<R>::combine(ws, m_eff, ws.c, out, st);
+    const bool final_basis = s_acc >= s_rem;
+    // outputs whose fraction this basis reaches
+    while (next < nf && (fr[next] <= s_done + s_acc * (1.0 + 1e-13) || (final_basis && next == nf - 1))) {
+      const double ds = (final_basis && next == nf - 1) ? s_acc : std::min(fr[next] - s_done, s_acc);
+      k_tridiag_coef<<<int(B), 64, 0, st>>>(m_eff, int(B), ws.theta, ws.Q, ws.beta0, zr, zi, nullptr, ds, ws.c);
+      count_launch();
+      Ops<R>::combine(ws, m_eff, ws.c, outs[next], st);
+      ++next;
+    }
+    if (next == nf) {
+      SYK_CUDA_CHECK(cudaGetLastError());
+      count_bases(1);
+      break;
+    }
+    if (!final_basis) {  // restart from the state at the end of this basis' step
+      k_tridiag_coef<<<int(B), 64, 0, st>>>(m_eff, int(B), ws.theta, ws.Q, ws.beta0, zr, zi, nullptr, s_acc, ws.c);
+      count_launch();
+      Ops<R>::combine(ws, m_eff, ws.c, outs[nf - 1], st);
+      cur = outs[nf - 1];
+    }
     SYK_CUDA_CHECK(cudaGetLastError());
     count_bases(1);
-    cur = out;
-    if (s_acc >= s_rem) s_rem = 0.0;
+    s_done += s_acc;
+    if (final_basis) s_rem = 0.0;
     else s_rem -= s_acc;
   }
   if (nsteps) *nsteps = steps;
@@ -710,8 +730,34 @@ int expmv_impl(const ApplyParams& P, int dtype, std::complex<double> z, const vo
     if (nsteps) *nsteps = 0;
     return SYK_OK;
   }
-  return dtype == SYK_C64 ? expmv_T<float>(P, dtype, z, psi, out, tol, ws, st, nsteps)
-                          : expmv_T<double>(P, dtype, z, psi, out, tol, ws, st, nsteps);
+  const double one = 1.0;
+  void* outs[1] = {out};
+  return dtype == SYK_C64 ? expmv_T<float>(P, dtype, z, psi, &one, 1, outs, tol, ws, st, nsteps)
+                          : expmv_T<double>(P, dtype, z, psi, &one, 1, outs, tol, ws, st, nsteps);
+}
+
+int expmv_points(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, const double* fr, int nf,
+                 void* const* outs, int64_t B, double tol, KrylovWS& ws, cudaStream_t st) {
+  if (ws.B != B || ws.D != P.D || ws.dtype != dtype) {
+    set_error("expmv: workspace shape mismatch");
+    return SYK_EINVAL;
+  }
+  if (nf < 1 || !(tol > 0.0) || !(fr[0] > 0.0)) {
+    set_error("expmv_points: need nf >= 1, tol > 0 and positive fractions");
+    return SYK_EINVAL;
+  }
+  for (int k = 1; k < nf; ++k)
+    if (!(fr[k] > fr[k - 1])) {
+      set_error("expmv_points: fractions must increase");
+      return SYK_EINVAL;
+    }
+  if (z == std::complex<double>(0.0, 0.0)) {
+    for (int k = 0; k < nf; ++k)
+      if (outs[k] != psi) SYK_CUDA_CHECK(cudaMemcpyAsync(outs[k], psi, ws.vec_bytes(), cudaMemcpyDeviceToDevice, st));
+    return SYK_OK;
+  }
+  return dtype == SYK_C64 ? expmv_T<float>(P, dtype, z, psi, fr, nf, outs, tol, ws, st, nullptr)
+                          : expmv_T<double>(P, dtype, z, psi, fr, nf, outs, tol, ws, st, nullptr);
 }
 
 namespace {

@@ -42,6 +42,12 @@ int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype
 int expmv_impl(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, void* out,
                int64_t B, double tol, KrylovWS& ws, cudaStream_t st, int* nsteps);
 
+// outs[k] = e^{fr[k] z H} psi for increasing fractions 0 < fr[0] < ... < fr[nf-1], each output
+// combined from the Krylov basis whose step covers it (no extra matvecs per output).  psi may
+// alias outs[nf-1] only; the other outputs must be distinct buffers.
+int expmv_points(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, const double* fr, int nf,
+                 void* const* outs, int64_t B, double tol, KrylovWS& ws, cudaStream_t st);
+
 // result[b] = sum_x conj(x[x][b]) y[x][b] (FP64), written to device memory `res` (B double2).
 int dot_columns(const void* x, const void* y, int64_t D, int64_t B, int dtype, KrylovWS& ws,
                 double2* res, cudaStream_t st);
