@@ -199,3 +199,23 @@ def test_apply_H_bench_size_launch_shapes(torch):
             y = syk.syk_apply_H(terms, sector, x).cpu().numpy().reshape(D, B)
             assert rel(y[rows], ref.reshape(len(rows), B)) < TOL["c64"], (sector, sh)
     syk.syk_autotune_reset()
+
+
+@pytest.mark.parametrize("B", [1, 8, 16])
+def test_apply_H_misaligned_vectors(torch, B):
+    """Vectors that start 8 bytes past a 16-byte boundary (views into a larger buffer): the
+    bulk-copy kernels need 16-byte alignment and decline, the row kernel computes the result."""
+    N = 20
+    J = inputs.couplings(N, 8)
+    terms = syk.syk_build_terms(N, J)
+    D = 1 << (N // 2 - 1)
+    psi = inputs.random_states(N, B, 12)
+    big = torch.zeros(D * B + 1, dtype=torch.complex64, device="cuda")
+    x = big[1:].view(D, B)
+    x.copy_(to_dev(torch, psi, "c64").view(D, B))
+    ybig = torch.zeros(D * B + 1, dtype=torch.complex64, device="cuda")
+    y = ybig[1:].view(D, B)
+    assert x.data_ptr() % 16 == 8 and y.data_ptr() % 16 == 8
+    syk.syk_apply_H(terms, 0, x, out=y)
+    ref = hm.H_sector_sparse(N, J, 0) @ psi.T
+    assert rel(y.cpu().numpy().reshape(D, B), ref.reshape(D, B)) < TOL["c64"]
