@@ -144,3 +144,31 @@ def test_otoc_N40_bench_parameters_c64_vs_c128(torch):
     b = syk.syk_otoc(terms, 10.0, 0, 1, ts, to_dev(torch, psi, "c64"), krylov_dim=40, tol=1e-7)
     assert rel(b / b[0], a / a[0]) < TOL["c64"]
     assert np.allclose(b[0] / b[0], 1.0)
+
+
+def test_G_N40_c64_vs_c128(torch):
+    """G(t) at full size (N = 40, sector 2^19, beta J = 5), two states: complex64 vectors with
+    FP64 scalars against the complex128 path; G(0) = 1/2 for every state."""
+    N = 40
+    J = inputs.couplings(N, 3)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 2, 3)
+    ts = [0.0, 1.0, 2.5]
+    a, Za = syk.syk_correlator_G(terms, 5.0, 2, ts, to_dev(torch, psi, "c128"), krylov_dim=40, tol=1e-12)
+    b, Zb = syk.syk_correlator_G(terms, 5.0, 2, ts, to_dev(torch, psi, "c64"), krylov_dim=40, tol=1e-7)
+    assert rel(b, a) < TOL["c64"]
+    assert rel(Zb, Za) < TOL["c64"]
+    assert np.abs(a[0] - 0.5).max() < 1e-12
+
+
+def test_otoc_unregularized_N40_c64_vs_c128(torch):
+    """The unregularized OTOC (rho split (0, 0, 0, 1)) at full size (N = 40, beta J = 10), two
+    states, t = 0 and 1.2: complex64 against complex128."""
+    N = 40
+    J = inputs.couplings(N, 4)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 2, 4)
+    x = (0.0, 0.0, 0.0, 1.0)
+    a = syk.syk_otoc_split(terms, 10.0, x, 0, 1, [0.0, 1.2], to_dev(torch, psi, "c128"), krylov_dim=40, tol=1e-12)
+    b = syk.syk_otoc_split(terms, 10.0, x, 0, 1, [0.0, 1.2], to_dev(torch, psi, "c64"), krylov_dim=40, tol=1e-7)
+    assert rel(b / b[0], a / a[0]) < TOL["c64"]
