@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--grad", action="store_true",
                     help="gradient workload: dF~(t*)/dJ for all couplings and dF~/dbeta at N=28, beta J=5, "
                          "t*=5, about 200 quadrature sub-intervals, 8 states, c64 and c128")
+    ap.add_argument("--grad-N", type=int, default=28, help="system size of the --grad workload")
+    ap.add_argument("--grad-t", type=float, default=5.0, help="t* of the --grad workload")
     return ap.parse_args()
 
 
@@ -471,7 +473,7 @@ def grad_main(a, rank, world, local_rank):
     from paper_2002_05725_gb300 import inputs, syk
     torch.cuda.set_device(local_rank)
     syk.load()
-    N, beta, tstar, states = 28, 5.0, 5.0, 8
+    N, beta, tstar, states = a.grad_N, 5.0, a.grad_t, 8
     quad_dz = 0.05  # |z| rho_est per Gauss-Legendre sub-interval: about 180 sub-intervals for t* = 5
     terms = syk.syk_build_terms(N, inputs.couplings(N, seed=0, realization=rank))
     psi = inputs.random_states(N, states, seed=0, realization=rank)
@@ -494,11 +496,11 @@ def grad_main(a, rank, world, local_rank):
     rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
     if rank == 0:
         print(json.dumps({
-            "metric": "gradient evaluations/hour at N=28 (all couplings and beta, one state each)",
+            "metric": f"gradient evaluations/hour at N={N} (all couplings and beta, one state each)",
             "value": world * states * 3600.0 / res["c64"]["seconds"], "unit": "gradients/hour", "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": res["c64"]["seconds"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": f"dF~(t*)/dJ_ijkl (C(28,4) = {inputs.n_terms(N)}) and dF~/dbeta, N=28, "
+            "config": {"workload": f"dF~(t*)/dJ_ijkl (C({N},4) = {inputs.n_terms(N)}) and dF~/dbeta, N={N}, "
                                    f"beta J={beta:g}, t*={tstar:g}, Gauss-Legendre sub-intervals of |z| rho_est <= {quad_dz:g}, "
                                    f"{states} states, Krylov 40", "N": N},
             "c128": {"seconds": ref["seconds"], "gradients_per_hour": states * 3600.0 / ref["seconds"],
