@@ -283,41 +283,47 @@ struct GradEngine {
     const int c = std::max(1, int(std::ceil(std::sqrt(double(S)))));
     const int nseg = (S + c - 1) / c;
     const std::complex<double> zs = z / double(S), zbar = std::conj(z);
-    std::vector<void*> ckpt(nseg), segbuf(c), node(4), lamq(4);
+    // per segment of up to c sub-intervals: the forward states at its 4c Gauss-Legendre nodes
+    // from one evolution of its checkpoint, and the adjoint at those nodes and at the segment's
+    // start from one evolution of the adjoint (states read off the Krylov bases at fractions of
+    // the step: no matvecs per node)
+    std::vector<void*> ckpt(nseg), nodeF(4 * c), nodeA(4 * c);
     for (auto& p : ckpt) SYK_TRY(get(&p));
-    for (auto& p : segbuf) SYK_TRY(get(&p));
-    for (auto& p : node) SYK_TRY(get(&p));
-    for (auto& p : lamq) SYK_TRY(get(&p));
-    // node fractions of a sub-interval, ascending, for the forward state (from its start) and
-    // for the adjoint (from its end: nodes 3..0, then the start of the sub-interval)
-    double ffwd[4], fadj[5];
-    for (int q = 0; q < 4; ++q) ffwd[q] = 0.5 * (1.0 + kGLx[q]);
-    for (int q = 0; q < 4; ++q) fadj[q] = 1.0 - ffwd[3 - q];
-    fadj[4] = 1.0;
+    for (auto& p : nodeF) SYK_TRY(get(&p));
+    for (auto& p : nodeA) SYK_TRY(get(&p));
+    std::vector<double> frf(4 * c), fra(4 * c + 1);
+    std::vector<void*> outa(4 * c + 1);
     // forward sweep: checkpoints psi(s/S) for s = 0, c, 2c, ...
     SYK_TRY(copy(ckpt[0], x));
     for (int sg = 1; sg < nseg; ++sg) {
       SYK_TRY(copy(ckpt[sg], ckpt[sg - 1]));
       SYK_TRY(expmv(sector, zs * double(c), ckpt[sg], ckpt[sg]));  // c sub-intervals in one evolution
     }
-    // backward: lam(v) marches from v = 1 to 0
+    // backward: the adjoint marches from v = 1 to 0, one segment at a time
     for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int s0 = sg * c, s1 = std::min(S, s0 + c);
-      SYK_TRY(copy(segbuf[0], ckpt[sg]));
-      for (int s = s0 + 1; s < s1; ++s) SYK_TRY(expmv(sector, zs, segbuf[s - s0 - 1], segbuf[s - s0]));
-      for (int s = s1 - 1; s >= s0; --s) {
-        // forward states at the 4 nodes of [s/S, (s+1)/S] from one evolution of segbuf[s]
-        SYK_TRY(expmv_points(sector, zs, segbuf[s - s0], ffwd, 4, node.data()));
-        // adjoint at the nodes (3 down to 0) and at s/S from one evolution of lam((s+1)/S)
-        void* aouts[5] = {lamq[3], lamq[2], lamq[1], lamq[0], lam};
-        SYK_TRY(expmv_points(sector, zbar / double(S), lam, fadj, 5, aouts));
-        for (int q = 3; q >= 0; --q) SYK_TRY(term_grad(sector, lamq[q], node[q], z * (0.5 * kGLw[q] / S), gJ));
-      }
+      const int s0 = sg * c, s1 = std::min(S, s0 + c), L = s1 - s0;
+      // forward nodes, ascending: sub-interval s, node q at fraction ((s - s0) + (1 + x_q)/2) / L
+      for (int s = s0; s < s1; ++s)
+        for (int q = 0; q < 4; ++q) frf[(s - s0) * 4 + q] = ((s - s0) + 0.5 * (1.0 + kGLx[q])) / L;
+      SYK_TRY(expmv_points(sector, zs * double(L), ckpt[sg], frf.data(), 4 * L, nodeF.data()));
+      // adjoint nodes by increasing distance from s1/S (s = s1-1 .. s0, q = 3 .. 0), then v = s0/S
+      int k = 0;
+      for (int s = s1 - 1; s >= s0; --s)
+        for (int q = 3; q >= 0; --q) {
+          fra[k] = ((s1 - s) - 0.5 * (1.0 + kGLx[q])) / L;
+          outa[k] = nodeA[(s - s0) * 4 + q];
+          ++k;
+        }
+      fra[k] = 1.0;
+      outa[k] = lam;
+      SYK_TRY(expmv_points(sector, zbar * (double(L) / S), lam, fra.data(), k + 1, outa.data()));
+      for (int s = s1 - 1; s >= s0; --s)
+        for (int q = 3; q >= 0; --q)
+          SYK_TRY(term_grad(sector, nodeA[(s - s0) * 4 + q], nodeF[(s - s0) * 4 + q], z * (0.5 * kGLw[q] / S), gJ));
     }
     for (auto p : ckpt) put(p);
-    for (auto p : segbuf) put(p);
-    for (auto p : node) put(p);
-    for (auto p : lamq) put(p);
+    for (auto p : nodeF) put(p);
+    for (auto p : nodeA) put(p);
     return SYK_OK;
   }
 
