@@ -36,25 +36,32 @@ __device__ __forceinline__ uint32_t grad_supp_bits(uint32_t xf, uint32_t s) {
 }
 
 // partial[((g*RC + chunk)*16 + s)*B + b] = sum over the chunk's rows of
-// conj(lam[x][b]) psi[x^m][b] (-1)^popcount(zeta & xf) (-1)^popcount(s & u(xf))
+// conj(lam[x][b]) psi[x^m][b] (-1)^popcount(zeta & xf) (-1)^popcount(s & u(xf)).
+// Each thread bins its rows' products by the support bits u in its own shared-memory slots
+// (bins[u][thread], conflict-free, one read-modify-write per row), applies the Walsh
+// transform over u to its bins once, and the threads of each column are then summed in a
+// fixed order: deterministic, and O(1) work per row instead of 2^k signed additions.
 template <typename R>
 __global__ void k_term_grad(const uint4* __restrict__ grec, int n, int sector, int64_t D, int B,
                             const typename CT<R>::T* __restrict__ lam, const typename CT<R>::T* __restrict__ psi,
                             double2* __restrict__ partial) {
   using C = typename CT<R>::T;
-  extern __shared__ double2 red[];
+  extern __shared__ __align__(16) unsigned char tg_smem[];
+  R* bins = reinterpret_cast<R*>(tg_smem);  // [32][NT]: real parts of u = 0..15, then imaginary parts
   const int g = blockIdx.x, chunk = blockIdx.y, RC = gridDim.y;
+  const int tid = threadIdx.x, NT = blockDim.x;
   const uint4 rec = __ldg(&grec[g]);
   const int k = (int)rec.w;
   const int ns = 1 << k;
-  const int b = threadIdx.x % B;
-  const int rows_per_pass = blockDim.x / B;
+  const int b = tid % B;
+  const int rows_per_pass = NT / B;
   const int64_t per = (D + RC - 1) / RC;
   const int64_t r0 = (int64_t)chunk * per, r1 = min(D, r0 + per);
-  R ar[16], ai[16];
-#pragma unroll
-  for (int s = 0; s < 16; ++s) ar[s] = ai[s] = R(0);
-  for (int64_t x = r0 + threadIdx.x / B; x < r1; x += rows_per_pass) {
+  for (int u = 0; u < ns; ++u) {
+    bins[u * NT + tid] = R(0);
+    bins[(16 + u) * NT + tid] = R(0);
+  }
+  for (int64_t x = r0 + tid / B; x < r1; x += rows_per_pass) {
     const uint32_t xc = (uint32_t)x;
     const uint32_t xf = xc | ((uint32_t)((__popc(xc) + sector) & 1) << (n - 1));
     const C l = lam[x * B + b];
@@ -66,26 +73,44 @@ __global__ void k_term_grad(const uint4* __restrict__ grec, int n, int sector, i
       ci = -ci;
     }
     const uint32_t u = grad_supp_bits(xf, rec.z) & (uint32_t)(ns - 1);
-#pragma unroll
-    for (int s = 0; s < 16; ++s)
-      if (s < ns) {
-        const bool neg = __popc((uint32_t)s & u) & 1;
-        ar[s] += neg ? -cr : cr;
-        ai[s] += neg ? -ci : ci;
-      }
+    bins[u * NT + tid] += cr;
+    bins[(16 + u) * NT + tid] += ci;
   }
-  for (int s = 0; s < ns; ++s) {
-    red[threadIdx.x] = make_double2((double)ar[s], (double)ai[s]);
-    __syncthreads();
-    if ((int)threadIdx.x < B) {
-      double sx = 0.0, sy = 0.0;
-      for (int t = threadIdx.x; t < (int)blockDim.x; t += B) {
-        sx += red[t].x;
-        sy += red[t].y;
+  // Walsh transform of this thread's bins: W_s = sum_u (-1)^popcount(s & u) bin_u
+  R hr[16], hi[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    hr[u] = u < ns ? bins[u * NT + tid] : R(0);
+    hi[u] = u < ns ? bins[(16 + u) * NT + tid] : R(0);
+  }
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1)  // in-place fast transform over the 4 bits (unused bins are 0)
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (!(u & h)) {
+        const R ar = hr[u], ai = hi[u], br = hr[u | h], bi = hi[u | h];
+        hr[u] = ar + br;
+        hi[u] = ai + bi;
+        hr[u | h] = ar - br;
+        hi[u | h] = ai - bi;
       }
-      partial[(((size_t)g * RC + chunk) * 16 + s) * B + threadIdx.x] = make_double2(sx, sy);
+  // bins u >= ns are zero, so for s < ns this is the transform over the group's k support bits
+#pragma unroll
+  for (int s = 0; s < 16; ++s)
+    if (s < ns) {
+      bins[s * NT + tid] = hr[s];
+      bins[(16 + s) * NT + tid] = hi[s];
     }
-    __syncthreads();
+  __syncthreads();
+  // column b's sum over its threads b, b + B, b + 2B, ... in increasing order
+  for (int o = tid; o < ns * B; o += NT) {
+    const int s = o / B, bb = o - s * B;
+    R sx = R(0), sy = R(0);
+    for (int j = 0; j < rows_per_pass; ++j) {
+      sx += bins[s * NT + bb + j * B];
+      sy += bins[(16 + s) * NT + bb + j * B];
+    }
+    partial[(((size_t)g * RC + chunk) * 16 + s) * B + bb] = make_double2((double)sx, (double)sy);
   }
 }
 
@@ -230,11 +255,19 @@ struct GradEngine {
   // acc[T][b] += coef * <lam|P_T|psi>
   int term_grad(int sector, const void* lam, const void* psi, std::complex<double> coef, double2* acc) {
     dim3 grid(terms->ngg, RC);
+    static bool smem_set = false;  // bins: 32 x (at most 256 threads) values of the vector type
+    if (!smem_set) {
+      SYK_CUDA_CHECK(cudaFuncSetAttribute(k_term_grad<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          32 * 256 * (int)sizeof(float)));
+      SYK_CUDA_CHECK(cudaFuncSetAttribute(k_term_grad<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          32 * 256 * (int)sizeof(double)));
+      smem_set = true;
+    }
     if (dtype == SYK_C64)
-      k_term_grad<float><<<grid, bdim, bdim * sizeof(double2), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
+      k_term_grad<float><<<grid, bdim, 32 * bdim * sizeof(float), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
                                                                      (const float2*)lam, (const float2*)psi, partial);
     else
-      k_term_grad<double><<<grid, bdim, bdim * sizeof(double2), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
+      k_term_grad<double><<<grid, bdim, 32 * bdim * sizeof(double), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
                                                                       (const double2*)lam, (const double2*)psi, partial);
     const int64_t n = terms->nterms * B;
     k_term_grad_accum<<<unsigned((n + 255) / 256), 256, 0, st>>>(terms->nterms, int(B), RC, terms->d_term_group,
