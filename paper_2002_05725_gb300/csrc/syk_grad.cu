@@ -225,7 +225,9 @@ struct GradEngine {
     SYK_TRY(krylov_ws_carve(&ws, w, wsb, D, dtype, krylov, B));
     bdim = int(B) * std::max(1, int(256 / B));
     const int64_t rows_per_pass = bdim / B;
-    RC = int(std::max<int64_t>(1, std::min<int64_t>(64, D / (rows_per_pass * 16))));
+    // row chunks of at least 64 rows per thread: the per-block epilogue (Walsh transform of the
+    // bins, column sums) then costs a fraction of the row loop
+    RC = int(std::max<int64_t>(1, std::min<int64_t>(64, D / (rows_per_pass * 64))));
     void* p = nullptr;
     SYK_TRY(alloc(&p, sizeof(double2) * size_t(terms->ngg) * RC * 16 * B));
     partial = static_cast<double2*>(p);
