@@ -102,3 +102,26 @@ def test_full_space_levels_match_dense_spectrum(N):
     assert np.allclose(got, full[:20], atol=1e-10)
     if N % 8 in (2, 6):  # either sector alone suffices
         assert np.allclose(rescale.full_space_levels(N, {1: distinct[1]}, 20), full[:20], atol=1e-10)
+
+
+def test_lyapunov_restricted_to_admissible_sizes():
+    """use_Ns restricts the extrapolation to the listed sizes: an outlier at a non-admissible
+    size then has no influence on the extrapolated lambda."""
+    lam, c = 0.7, 0.3
+    Ns = [20, 24, 28, 32, 36]
+    t = np.linspace(0.0, 15.0, 30001)
+    Ft = {N: 1.0 - (c / N) * np.exp(lam * t) for N in Ns}
+    Ft[24] = 1.0 - (2 * c / 24) * np.exp(lam * t)  # size 24 off the scaling family
+    bad = rescale.lyapunov(Ns, t, Ft, 1.8)
+    good = rescale.lyapunov(Ns, t, Ft, 1.8, use_Ns=[32, 36])
+    assert abs(bad["lambda"] - lam) > 1e-2
+    assert good["fit_N"] == [32.0, 36.0] and abs(good["lambda"] - lam) < 1e-4
+
+
+def test_sector_levels_needed_by_N_mod_8():
+    assert rescale.sector_levels_needed(40) == ((0, 1), 20)   # 0 mod 8: no degeneracy
+    assert rescale.sector_levels_needed(36) == ((0, 1), 10)   # 4 mod 8: pairs within sectors
+    assert rescale.sector_levels_needed(34) == ((0,), 10)     # 2 mod 8: sectors are copies
+    assert rescale.sector_levels_needed(38) == ((0,), 10)     # 6 mod 8
+    with pytest.raises(ValueError):
+        rescale.full_space_levels(40, {0: np.zeros(20)}, 20)  # both sectors needed
