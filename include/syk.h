@@ -125,7 +125,9 @@ int syk_expmv(const syk_terms* terms, int parity, int dtype, double z_re, double
  * front and must not fail with out-of-memory mid-run, hosts that route every
  * device allocation through their own pool, and latency-critical loops where
  * cudaMalloc/cudaFree would stall or synchronise the device.  It calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * cudaMalloc, cudaFree or other allocating routine, and unlike syk_expmv it
+ * never records or instantiates CUDA graphs of its Lanczos iterations (an
+ * instantiated graph takes device memory): every kernel is launched directly.
  * Limit: the scratch array is SYK_STATIC_SCRATCH_BYTES (16 MiB) of static
  * device memory, held by every GPU that loads the library until the process
  * exits; a call whose syk_workspace_bytes(N, dtype, krylov_dim, batch, 0)
@@ -279,6 +281,15 @@ int syk_autotune_reset(void);
 /* ------------------------------------------------------------- diagnostics
  * syk_last_error -- message of the last failed call on this thread ("" if none). */
 const char* syk_last_error(void);
+
+/* syk_fma_peak -- measured FMA throughput of the current device, the roofline of the
+ * matvec (one complex multiply-add, 4 real FMA, per nonzero of H and state: FP32 for
+ * SYK_C64, FP64 for SYK_C128).  The paper has no counterpart; this is measurement.  Runs
+ * `iters` x 128 dependent FMA (8 independent chains) in each of 4 x 256 threads per SM,
+ * timed with CUDA events on `stream` after one short warm-up launch.  bits: 32 or 64.
+ * Outputs (host, any may be NULL): *tflops = 2 x FMA / time, *sms = the device's SM count
+ * (cudaDevAttrMultiProcessorCount), *ms = the timed launch.  Synchronises `stream`. */
+int syk_fma_peak(int bits, int iters, double* tflops, int* sms, double* ms, void* stream);
 
 /* syk_counters -- counters since the last reset (any pointer may be NULL):
  * H applications per state (a batch of B states counts B), Krylov bases, and

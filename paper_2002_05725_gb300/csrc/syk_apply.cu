@@ -167,7 +167,7 @@ void launch_one(const ApplyParams& p, const void* psi, void* y, int64_t ld, int6
   using C = typename CT<R>::T;
   const int threads = 128;
   int64_t blocks = (p.D + threads - 1) / threads;
-  blocks = std::min<int64_t>(blocks, 152 * 64);
+  blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 64);
   k_apply_rows<R, BT><<<(unsigned)blocks, threads, 0, st>>>(p, static_cast<const C*>(psi), static_cast<C*>(y), ld, b0);
   count_launch();
 }
@@ -433,7 +433,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
       if ((int64_t(1) << (var + vntb)) <= p.D) {
         const int64_t nt = p.D >> (var + vntb);
         int vcs = 1;
-        while (vcs < 8 && nt * vcs * ((1 << vntb) / 32) < 152 * 32) vcs *= 2;
+        while (vcs < 8 && nt * vcs * ((1 << vntb) / 32) < sm_count() * 32) vcs *= 2;
         const int rc = launch_coset_var(p, BT, psi, y, st, var, vntb, vcs);
         if (rc <= 0) return rc;
       }
@@ -448,7 +448,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     // few warps, the mask chunks of a tile are split across a cluster of CTAs
     while (ntb > 6 && (p.D < ((int64_t)Cfg::RPT << ntb) || Cfg::smem(Cfg::RPT << ntb) > 80 * 1024)) --ntb;
     const int64_t nt = p.D / ((int64_t)Cfg::RPT << ntb);
-    while (cs < 8 && nt * cs * ((1 << ntb) / 32) < 152 * 32) cs *= 2;
+    while (cs < 8 && nt * cs * ((1 << ntb) / 32) < sm_count() * 32) cs *= 2;
   }
   const int T = Cfg::RPT << ntb;
   if (p.D < T) return 1;
@@ -463,14 +463,8 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     SYK_TRY(tile_groups(p.terms, tb, Cfg::GMAX, &groups, &ng));
   }
   const size_t smem = Cfg::smem(T);
-  static size_t attr_set = 0;  // per instantiation: largest dynamic smem enabled so far
-  if (smem > attr_set) {
-    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Cfg::smem(Cfg::RPT << 8)));
-    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_tiled<R, BT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Cfg::smem(Cfg::RPT << 8)));
-    attr_set = Cfg::smem(Cfg::RPT << 8);
-  }
+  SYK_TRY(ensure_smem_limit((const void*)k_apply_tiled<R, BT, false>, (int)Cfg::smem(Cfg::RPT << 8)));
+  SYK_TRY(ensure_smem_limit((const void*)k_apply_tiled<R, BT, true>, (int)Cfg::smem(Cfg::RPT << 8)));
   if (cs == 1) {
     k_apply_tiled<R, BT, false><<<(unsigned)ntiles, 1u << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
                                                                      static_cast<C*>(y));
@@ -557,7 +551,7 @@ int launch_apply_chi(int N, int i, int parity_in, int dtype, const void* psi, vo
   const int n = N / 2;
   const int64_t D = int64_t(1) << (n - 1);
   const int threads = 256;
-  int64_t blocks = std::min<int64_t>((D * batch + threads - 1) / threads, 152 * 32);
+  int64_t blocks = std::min<int64_t>((D * batch + threads - 1) / threads, (int64_t)sm_count() * 32);
   if (dtype == SYK_C64)
     k_apply_chi<float><<<(unsigned)blocks, threads, 0, st>>>(n, i, 1 - parity_in, D, batch,
                                                              static_cast<const float2*>(psi), static_cast<float2*>(y));

@@ -269,14 +269,8 @@ int launch_coset_ntb(const ApplyParams& p, const CosetLayout* L, const void* psi
   const int64_t ntiles = p.D / T;
   const size_t smem = Cfg::smem(T);
   if (smem > kMaxSmemPerCta) return 1;
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_coset<BT, RB, false, NTB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    SYK_CUDA_CHECK(cudaFuncSetAttribute(k_apply_coset<BT, RB, true, NTB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    attr_set = true;
-  }
+  SYK_TRY(ensure_smem_limit((const void*)k_apply_coset<BT, RB, false, NTB>, (int)smem));
+  SYK_TRY(ensure_smem_limit((const void*)k_apply_coset<BT, RB, true, NTB>, (int)smem));
   const float2* x = static_cast<const float2*>(psi);
   float2* out = static_cast<float2*>(y);
   if (cs == 1) {

@@ -257,14 +257,9 @@ struct GradEngine {
   // acc[T][b] += coef * <lam|P_T|psi>
   int term_grad(int sector, const void* lam, const void* psi, std::complex<double> coef, double2* acc) {
     dim3 grid(terms->ngg, RC);
-    static bool smem_set = false;  // bins: 32 x (at most 256 threads) values of the vector type
-    if (!smem_set) {
-      SYK_CUDA_CHECK(cudaFuncSetAttribute(k_term_grad<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          32 * 256 * (int)sizeof(float)));
-      SYK_CUDA_CHECK(cudaFuncSetAttribute(k_term_grad<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          32 * 256 * (int)sizeof(double)));
-      smem_set = true;
-    }
+    // bins: 32 x (at most 256 threads) values of the vector type
+    SYK_TRY(ensure_smem_limit((const void*)k_term_grad<float>, 32 * 256 * (int)sizeof(float)));
+    SYK_TRY(ensure_smem_limit((const void*)k_term_grad<double>, 32 * 256 * (int)sizeof(double)));
     if (dtype == SYK_C64)
       k_term_grad<float><<<grid, bdim, 32 * bdim * sizeof(float), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
                                                                      (const float2*)lam, (const float2*)psi, partial);

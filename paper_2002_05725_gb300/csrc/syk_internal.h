@@ -130,6 +130,12 @@ uint64_t graph_epoch();  // changes whenever captured graphs may hold stale para
 void bump_graph_epoch();
 bool graphs_enabled();
 
+// Raises func's dynamic shared-memory limit to at least `bytes` on the current device (the
+// attribute is per device; done once per kernel and device, thread-safe).
+int ensure_smem_limit(const void* func, int bytes);
+// Streaming multiprocessors of the current device (cached per device; 1 if the query fails).
+int sm_count();
+
 inline size_t dtype_size(int dtype) { return dtype == SYK_C64 ? 8 : 16; }
 inline bool dtype_ok(int dtype) { return dtype == SYK_C64 || dtype == SYK_C128; }
 

@@ -24,12 +24,14 @@
 namespace syk {
 namespace {
 
-constexpr int kMaxRedBlocks = 304;  // 2 x 152 SMs
+// Reduction kernels run 2 blocks per SM of the current device; workspaces are sized for up to
+// kRedBlocksCap blocks so that their size does not depend on the device.
+constexpr int kRedBlocksCap = 512;
 constexpr int kFlush = 16;          // FP32 partial sums are flushed to FP64 every kFlush elements
 
 inline int vec_bdim(int64_t B) { return int(B) * std::max(1, int(256 / B)); }
-inline int red_grid(int64_t total, int bdim) {
-  return int(std::min<int64_t>((total + bdim - 1) / bdim, kMaxRedBlocks));
+inline int red_grid(int64_t total, int bdim, int max_blocks) {
+  return int(std::min<int64_t>((total + bdim - 1) / bdim, max_blocks));
 }
 
 // ---------------------------------------------------------------- reductions
@@ -428,7 +430,7 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 // ---------------------------------------------------------------- workspace
 size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B) {
   const int bdim = vec_bdim(B);
-  const int G = red_grid(D * B, bdim);
+  const int G = red_grid(D * B, bdim, kRedBlocksCap);
   const size_t vb = align_up(size_t(D) * B * dtype_size(dtype));
   size_t s = 0;
   s += vb * (m + 1);                                  // V
@@ -460,7 +462,7 @@ int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype
   ws->D = D;
   ws->dtype = dtype;
   ws->bdim = vec_bdim(B);
-  ws->G = red_grid(D * B, ws->bdim);
+  ws->G = red_grid(D * B, ws->bdim, std::min(kRedBlocksCap, 2 * sm_count()));
   const size_t vb = align_up(size_t(D) * B * dtype_size(dtype));
   char* p = static_cast<char*>(base);
   auto take = [&](size_t n) {
@@ -538,7 +540,9 @@ thread_local GraphCache t_cache;
 template <typename F>
 int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int64_t B, int m, int j0, int j1,
                         bool two, cudaStream_t st, F&& eager) {
-  if (!graphs_enabled() || prof_enabled()) return eager(st);
+  // no_alloc callers (syk_expmv_static) always launch eagerly: capturing and instantiating a
+  // graph, and the cache's host containers, would allocate
+  if (P.no_alloc || !graphs_enabled() || prof_enabled()) return eager(st);
   const SegKey key{ws.V, P.m4_tab, P.sector, dtype, B, P.D, m, j0, j1, two ? 1 : 0, graph_epoch()};
   auto it = t_cache.graphs.find(key);
   if (it == t_cache.graphs.end()) {

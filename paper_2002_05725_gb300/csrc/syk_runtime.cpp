@@ -2,6 +2,7 @@
 // apply_H launch, and a pinned host staging buffer for small device reads.
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -110,6 +111,30 @@ void prof_collect() {
     }
   }
   p.pending.resize(keep);
+}
+
+int ensure_smem_limit(const void* func, int bytes) {
+  static std::mutex mtx;
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> limit set
+  int dev = -1;
+  SYK_CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mtx);
+  int& cur = done[{func, dev}];
+  if (bytes <= cur) return SYK_OK;
+  SYK_CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  cur = bytes;
+  return SYK_OK;
+}
+
+int sm_count() {
+  static std::atomic<int> cache[128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return 1;
+  int v = cache[dev].load();
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+  cache[dev] = v;
+  return v;
 }
 
 void* pinned_scratch(size_t bytes) {

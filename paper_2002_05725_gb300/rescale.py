@@ -152,19 +152,22 @@ def lyapunov(Ns, t, Ft_by_N: dict, beta: float, F0: float = 0.25, level=None, de
     """The whole procedure on disorder-averaged curves Ft_by_N[N] (on the common grid t).
 
     level defaults to 1 - F0; degree to 2 for beta >= 5.6 and 1 below; use_Ns restricts the
-    extrapolation to those sizes (e.g. `admissible(...)`), default all."""
+    procedure to those sizes (e.g. `admissible(...)`), default all: only they enter the pairs
+    of lambda_fit and the extrapolation (t* is still reported for every size)."""
     lev = 1.0 - F0 if level is None else float(level)
     Ns = sorted(int(N) for N in Ns)
     tstar = [crossing_time(t, Ft_by_N[N], lev) for N in Ns]
     if any(math.isnan(x) for x in tstar):
         missing = [N for N, x in zip(Ns, tstar) if math.isnan(x)]
         raise ValueError(f"F~ never reaches {lev} for N = {missing}: extend the time grid")
-    Nk, lam = lambda_fit(Ns, tstar)
+    keep = Ns if use_Ns is None else [N for N in Ns if N in {int(u) for u in use_Ns}]
+    if len(keep) < 2:
+        raise ValueError(f"lambda_fit needs at least two sizes, got {keep}")
+    Nk, lam = lambda_fit(keep, [ts for N, ts in zip(Ns, tstar) if N in keep])
     deg = (2 if beta >= 5.6 else 1) if degree is None else int(degree)
-    sel = np.ones(len(Nk), dtype=bool) if use_Ns is None else np.isin(Nk, np.asarray(use_Ns, dtype=np.float64))
-    lam0, se, coef = extrapolate(Nk[sel], lam[sel], deg)
+    lam0, se, coef = extrapolate(Nk, lam, deg)
     return {"beta": beta, "level": lev, "N": Ns, "t_star": tstar, "lambda_fit_N": Nk.tolist(),
-            "lambda_fit": lam.tolist(), "degree": deg, "fit_N": Nk[sel].tolist(), "lambda": lam0,
+            "lambda_fit": lam.tolist(), "degree": deg, "fit_N": Nk.tolist(), "lambda": lam0,
             "lambda_stderr": se, "coefficients": coef.tolist()}
 
 

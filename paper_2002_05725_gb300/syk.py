@@ -74,6 +74,7 @@ def load(build_if_missing: bool = False):
         "syk_autotune_import": (i32, [ctypes.c_char_p]),
         "syk_autotune_reset": (i32, []),
         "syk_lowest_eigenvalues": (i32, [vp, i32, i32, vp, i32, i32, dbl, vp, vp, vp, vp]),
+        "syk_fma_peak": (i32, [i32, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -90,7 +91,7 @@ def exported_symbols():
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
-            "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues"]
+            "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak"]
 
 
 def _check(rc: int, what: str):
@@ -421,3 +422,13 @@ def syk_correlator_G_imag(terms: Terms, beta: float, i: int, taus, psi0, krylov_
            "syk_correlator_G_imag")
     del keep
     return G[..., 0] + 1j * G[..., 1], Z
+
+
+def syk_fma_peak(bits: int = 32, iters: int = 4096, stream=None):
+    """Measured FMA throughput of the current device: {"tflops", "sms", "ms"} (2 flop per FMA)."""
+    L = load()
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    sms = ctypes.c_int(0)
+    _check(L.syk_fma_peak(int(bits), int(iters), ctypes.byref(tf), ctypes.byref(sms), ctypes.byref(ms),
+                          _stream(stream)), "syk_fma_peak")
+    return {"tflops": tf.value, "sms": sms.value, "ms": ms.value}

@@ -113,9 +113,27 @@ def test_lyapunov_restricted_to_admissible_sizes():
     Ft = {N: 1.0 - (c / N) * np.exp(lam * t) for N in Ns}
     Ft[24] = 1.0 - (2 * c / 24) * np.exp(lam * t)  # size 24 off the scaling family
     bad = rescale.lyapunov(Ns, t, Ft, 1.8)
-    good = rescale.lyapunov(Ns, t, Ft, 1.8, use_Ns=[32, 36])
+    good = rescale.lyapunov(Ns, t, Ft, 1.8, use_Ns=[28, 32, 36])
     assert abs(bad["lambda"] - lam) > 1e-2
     assert good["fit_N"] == [32.0, 36.0] and abs(good["lambda"] - lam) < 1e-4
+
+
+def test_lyapunov_pairs_only_admissible_sizes():
+    """An admissible size whose lower neighbour is not admissible is paired with the next
+    admissible size below it, never with the outlier: with the outlier at 28 and sizes 20, 32,
+    36 admissible, lambda_fit(32) comes from (20, 32) and is exact for the scaling family."""
+    lam, c = 0.7, 0.3
+    Ns = [20, 24, 28, 32, 36]
+    t = np.linspace(0.0, 15.0, 30001)
+    Ft = {N: 1.0 - (c / N) * np.exp(lam * t) for N in Ns}
+    Ft[28] = 1.0 - (3 * c / 28) * np.exp(lam * t)  # size 28 off the scaling family
+    res = rescale.lyapunov(Ns, t, Ft, 1.8, use_Ns=[20, 32, 36])
+    assert res["fit_N"] == [32.0, 36.0]
+    assert np.allclose(res["lambda_fit"], lam, rtol=1e-4)
+    assert abs(res["lambda"] - lam) < 1e-4
+    assert len(res["t_star"]) == len(Ns)
+    with pytest.raises(ValueError):
+        rescale.lyapunov(Ns, t, Ft, 1.8, use_Ns=[36])
 
 
 def test_sector_levels_needed_by_N_mod_8():

@@ -20,7 +20,10 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dt", ["c128", "c64"])
-def test_expmv_static_matches_expmv_twice(dt):
+def test_expmv_static_matches_expmv_repeatedly(dt):
+    """Three calls in a row agree with syk_expmv, and calls after the first take no device
+    memory: the first call may still load the library's device code (lazy module loading)
+    and look up the array's address, later ones must not capture or instantiate graphs."""
     torch = torch_or_skip()
     lib = syk.load(build_if_missing=True)
     N, B, m = 20, 4, 30
@@ -33,15 +36,20 @@ def test_expmv_static_matches_expmv_twice(dt):
     ref, _ = syk.syk_expmv(terms, 1, z, psi, krylov_dim=m, tol=tol)
     ref = ref.cpu().numpy()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for call in range(2):
-        out = torch.full_like(psi, complex(float("nan"), float("nan")))
+    outs = [torch.empty_like(psi) for _ in range(3)]
+    torch.cuda.synchronize()
+    free = []
+    for call, out in enumerate(outs):
+        out.fill_(complex(float("nan"), float("nan")))
         nsteps = ctypes.c_int(0)
         rc = lib.syk_expmv_static(terms.ptr, 1, code, z.real, z.imag, psi.data_ptr(), out.data_ptr(), B, m, tol,
                                   stream, ctypes.byref(nsteps))
         assert rc == syk.SYK_OK, lib.syk_last_error()
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         assert nsteps.value >= 1
         assert rel(out.cpu().numpy(), ref) < TOL[dt], (call, rel(out.cpu().numpy(), ref))
+    assert free[1] == free[2], free
 
 
 def test_expmv_static_rejects_oversize_and_unuploaded_terms():
