@@ -32,7 +32,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP32_LANES_PER_SM = 128
-N_SM = 152
 
 
 def parse():
@@ -61,6 +60,11 @@ def parse():
                          "t*=5, about 200 quadrature sub-intervals, 8 states, c64 and c128")
     ap.add_argument("--grad-N", type=int, default=28, help="system size of the --grad workload")
     ap.add_argument("--grad-t", type=float, default=5.0, help="t* of the --grad workload")
+    ap.add_argument("--c128-states", type=int, default=2,
+                    help="states of the timed complex64 batch also evaluated in the plain complex128 form "
+                         "(one state per step), for the c128 arm of the metric and the c64 accuracy (0: skip)")
+    ap.add_argument("--no-batched-extra", action="store_true",
+                    help="skip the mixed-N batch figure that the default line carries")
     return ap.parse_args()
 
 
@@ -110,9 +114,16 @@ def ncu_traffic(N, states, dtype, kind="tiled", source="syk_apply.cu"):
     return out, os.path.relpath(path, ROOT)
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x clock."""
-    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, n_sm):
+    """FP32 FMA peak from unit counts: SMs x 128 lanes x 2 flop x clock."""
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def curve_error(F, Fref):
+    """Largest over states of max_t |F~ - F~ref| / max_t |F~ref| with F~ = F / F(t=0)."""
+    a = np.asarray(F) / np.asarray(F)[0]
+    b = np.asarray(Fref) / np.asarray(Fref)[0]
+    return float(np.max(np.max(np.abs(a - b), axis=0) / np.max(np.abs(b), axis=0)))
 
 
 # ------------------------------------------------------------------ cost model
@@ -290,6 +301,44 @@ def curves_per_hour(world, states, steps, t_max_ms):
 
 
 # ------------------------------------------------------------------ GPU arm
+def c128_plain_arm(a, terms, host, times, dev, F64):
+    """The plain complex128 form (the paper's precision) of the same curves: one state per
+    step, states 0..K-1 of the timed batch.  Returns the c128 arm and the accuracy of the
+    timed complex64 curves of those states against it."""
+    import torch
+
+    from paper_2002_05725_gb300 import syk
+    K = min(a.c128_states, a.states)
+    cols = [torch.from_numpy(np.ascontiguousarray(host[s][:, None])).to(torch.complex128).to(dev) for s in range(K)]
+    stream = torch.cuda.current_stream(dev)
+    syk.syk_autotune_apply(terms, syk.SYK_C128, 1)
+    syk.syk_otoc(terms, a.beta, 0, 1, times[:2], cols[0], krylov_dim=a.krylov, tol=1e-12)  # warm-up
+    torch.cuda.synchronize(dev)
+    syk.syk_counters(reset=True)
+    clk = ClockSampler(dev.index)
+    clk.start()
+    total_ms, curves = 0.0, []
+    for x in cols:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        curves.append(syk.syk_otoc(terms, a.beta, 0, 1, times, x, krylov_dim=a.krylov, tol=1e-12))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += e0.elapsed_time(e1)
+    clocks = clk.stop()
+    cnt = syk.syk_counters(reset=True)
+    F128 = np.concatenate(curves, axis=1)
+    arm = {"value": K * 3600.0 / (total_ms / 1e3), "unit": "curves/hour", "steps": K, "states_per_step": 1,
+           "ms_per_step": total_ms / K, "dtype": "c128", "tol": 1e-12,
+           "applies_per_curve": cnt["h_applies"] / K, "clocks": clocks,
+           "note": "same coupling draw, grid and Krylov dimension; one state per step; untimed warm-up of "
+                   "two points; L2 not flushed (each step runs for seconds)"}
+    acc = {"max_t_rel_err_c64_vs_c128": curve_error(F64[:, :K], F128), "states": K, "bound": 1e-5,
+           "definition": "per state max_t |F~_c64 - F~_c128| / max_t |F~_c128|, largest over the states; "
+                         "F~_c64 from the last timed complex64 step"}
+    return arm, acc
+
+
 def gpu_main(a, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -308,6 +357,7 @@ def gpu_main(a, rank, world, local_rank):
     psi_dev = psi_host.to(dev).contiguous()
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     # untimed: pick the matvec launch shape for this (N, dtype, batch)
     code = syk.SYK_C64 if a.dtype == "c64" else syk.SYK_C128
     if a.states in (1, 2, 4, 8, 16):
@@ -324,10 +374,13 @@ def gpu_main(a, rank, world, local_rank):
 
     for _ in range(a.warmup):
         F = step(psi_dev)
+    # the matvec's roofline: FMA throughput measured on this device just before the timed region
+    fma = {32: syk.syk_fma_peak(32, 8192), 64: syk.syk_fma_peak(64, 256)}
     barrier()
 
     # timed region: device-resident inputs
     syk.syk_counters(reset=True)
+    syk.syk_matvec_launches(reset=True)
     syk.syk_profile_read(reset=True)
     syk.syk_profile_enable(True)
     clk = ClockSampler(local_rank)
@@ -345,6 +398,8 @@ def gpu_main(a, rank, world, local_rank):
     syk.syk_profile_enable(False)
     prof = syk.syk_profile_read(reset=True)
     cnt = syk.syk_counters(reset=True)
+    mv = syk.syk_matvec_launches(reset=True)
+    F_timed = F
     barrier()
     t_max = max_over_ranks(total_ms, dev, world)
     value = curves_per_hour(world, a.states, a.steps, t_max)
@@ -362,7 +417,7 @@ def gpu_main(a, rank, world, local_rank):
 
     if rank != 0:
         return
-    Ft = F / F[0]
+    Ft = F_timed / F_timed[0]
     applies_per_state = cnt["h_applies"] / max(1, a.steps) / a.states
     D = terms.D
     nnz = D * terms.nmasks
@@ -370,9 +425,9 @@ def gpu_main(a, rank, world, local_rank):
     flops = 8.0 * nnz * a.states
     pk, pk_kind = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    bound, unit, peak = "alu", "TFLOP/s", fp32_peak_tflops(sm_mhz)
-    if a.dtype == "c128":
-        peak = peak / 64.0  # FP64 FMA rate of GB300 is 1/64 of FP32
+    bits = 32 if a.dtype == "c64" else 64
+    peak = fma[bits]["tflops"]
+    derived = fp32_peak_tflops(sm_mhz, n_sm) / (1.0 if bits == 32 else 64.0)
     achieved = flops / (avg_ms * 1e-3) / 1e12
     tile = next((e for e in tuned if e["N"] == a.N and e["batch"] == a.states and e["dtype"] == code), None)
     kname, kind, ksrc = matvec_kernel(tile, a.states, a.dtype)
@@ -382,11 +437,11 @@ def gpu_main(a, rank, world, local_rank):
     if ncu_vals and "smem_wavefronts_per_launch" in ncu_vals:
         # the matvec's binding unit: the SMs' shared-memory port (128 B per cycle per SM)
         sbytes = ncu_vals["smem_wavefronts_per_launch"] * 128 + ncu_vals.get("tma_fill_bytes_per_launch", 0.0)
-        speak = N_SM * 128 * sm_mhz * 1e6 / 1e9
+        speak = n_sm * 128 * sm_mhz * 1e6 / 1e9
         sach = sbytes / (avg_ms * 1e-3) / 1e9
         smem = {"achieved": sach, "peak": speak, "unit": "GB/s", "frac": sach / speak, "bytes": sbytes,
                 "source": "ncu LSU shared-memory wavefronts x 128 B + bulk-copy fill bytes, per launch",
-                "peak_kind": f"derived: {N_SM} SMs x 128 B/cycle x {sm_mhz:.0f} MHz"}
+                "peak_kind": f"derived: {n_sm} SMs x 128 B/cycle x {sm_mhz:.0f} MHz"}
     esz = 8 if a.dtype == "c64" else 16
     gather = nnz * a.states * esz / (avg_ms * 1e-3) / 1e9
     line = {
@@ -394,15 +449,20 @@ def gpu_main(a, rank, world, local_rank):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
         "config": config_dict(a, times),
-        "roofline": {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
-                     "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz"
-                                  + (" / 64 (FP64)" if a.dtype == "c128" else ""),
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                     "peak_kind": f"measured: syk_fma_peak({bits}) on this device before the timed region "
+                                  f"({'FFMA' if bits == 32 else 'DFMA'} chains, {n_sm} SMs, "
+                                  f"{fma[bits]['ms']:.2f} ms); unit-count figure {derived:.2f} TFLOP/s at "
+                                  f"{sm_mhz:.0f} MHz",
+                     "fma_peaks_measured": {"fp32_tflops": fma[32]["tflops"], "fp64_tflops": fma[64]["tflops"],
+                                            "sms": n_sm},
                      "per_launch": {"flops": flops, "avg_ms": avg_ms, "launches": prof["launches"]},
                      "shared_memory": smem},
         "hpsi": {"gather_GBps": gather, "hbm_peak_GBps": pk.get("hbm_gbs"), "gather_frac_of_hbm":
                  gather / float(pk.get("hbm_gbs", 6800.0)), "peak_kind": pk_kind},
         "apply_tile": tile,
+        "matvec_launches_by_kernel": mv,
         "applies_per_curve": applies_per_state,
         "applies_per_curve_model": applies_model(a.N, a.beta, times[1:], a.krylov, a.tol),
         "krylov_bases_per_step": cnt["krylov_bases"] / max(1, a.steps),
@@ -412,6 +472,10 @@ def gpu_main(a, rank, world, local_rank):
                 "d2h_bytes_per_step": int(len(times) * a.states * 16)},
         "result_check": {"Ftilde_t0": float(np.real(Ft[0, 0])), "Ftilde_tmax_mean": float(np.mean(np.real(Ft[-1])))},
     }
+    if world == 1 and a.dtype == "c64" and a.c128_states > 0:
+        line["c128_plain"], line["accuracy"] = c128_plain_arm(a, terms, host, times, dev, F_timed)
+    if world == 1 and not a.no_batched_extra:
+        line["batched"] = run_batched(a, 0, 1, local_rank, draws=1)
     if not a.no_cpu_baseline and world == 1:
         per_apply, info = oracle_apply_seconds(a.N, a.states, a.cpu_seconds)
         curve_s = per_apply * applies_per_state
@@ -423,8 +487,9 @@ def gpu_main(a, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def batched_main(a, rank, world, local_rank):
-    """Mixed-N batch: draws x (N in 20..40) x (beta J in 1, 3, 10), 8 states each, 10 points to t=12."""
+def run_batched(a, rank, world, local_rank, draws):
+    """Mixed-N batch: draws x (N in 20..40) x (beta J in 1, 3, 10), 8 states each, 10 points to t=12.
+    Returns the throughput figure (curves/hour over the wall time of one syk_otoc_batch call)."""
     import torch
 
     from paper_2002_05725_gb300 import inputs, syk
@@ -433,7 +498,7 @@ def batched_main(a, rank, world, local_rank):
     times = time_grid(a.npts, a.tmax)
     Ns, betas = [20, 24, 28, 32, 36, 40], [1.0, 3.0, 10.0]
     items = []
-    for d in range(a.draws):
+    for d in range(draws):
         for N in Ns:
             for b in betas:
                 r = rank * 100000 + d * 100 + N
@@ -451,18 +516,24 @@ def batched_main(a, rank, world, local_rank):
     wall = time.perf_counter() - t0
     cnt = syk.syk_counters(reset=True)
     curves = 8 * len(items)
-    if rank == 0:
-        print(json.dumps({
-            "metric": "OTOC curves/hour, mixed-N batch", "value": world * curves * 3600.0 / wall,
-            "unit": "curves/hour", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": f"{a.draws} draw(s) x N in {Ns} x beta J in {betas}, 8 states each, "
+    return {"metric": "OTOC curves/hour, mixed-N batch", "value": world * curves * 3600.0 / wall,
+            "unit": "curves/hour", "wall_s": wall, "dtype": "c64",
+            "config": {"workload": f"{draws} draw(s) x N in {Ns} x beta J in {betas}, 8 states each, "
                                    f"F~ at t=0 and {a.npts} points to t={a.tmax:g}, Krylov {a.krylov}, "
                                    f"tol {a.tol:g}, {a.workers} host workers / streams",
                        "items": len(items), "curves": curves},
             "gpu_launches": cnt["launches"], "h_applies": cnt["h_applies"],
-            "result_check": {"Ftilde_t0_all_one": bool(all(np.allclose(F[0] / F[0], 1) for F in out))}}),
-            flush=True)
+            "result_check": {"Ftilde_t0_all_one": bool(all(np.allclose(F[0] / F[0], 1) for F in out))}}
+
+
+def batched_main(a, rank, world, local_rank):
+    res = run_batched(a, rank, world, local_rank, a.draws)
+    if rank == 0:
+        line = {"metric": res["metric"], "value": res["value"], "unit": res["unit"], "n_gpus": world, "steps": 1,
+                "warmup": 1, "ms_per_step": res["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64", "data": "synthetic"}
+        line.update({k: v for k, v in res.items() if k not in line and k not in ("metric", "wall_s")})
+        print(json.dumps(line), flush=True)
 
 
 def grad_main(a, rank, world, local_rank):

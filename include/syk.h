@@ -296,6 +296,12 @@ int syk_fma_peak(int bits, int iters, double* tflops, int* sms, double* ms, void
  * kernel launches made by the library.  reset != 0 zeroes them after reading. */
 int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int64_t* launches, int reset);
 
+/* syk_matvec_launches -- matvec launches since the last reset by kernel family (any
+ * pointer may be NULL): the row kernel (small sectors, other batch sizes, unaligned
+ * vectors), the tiled kernel and the complex64 coset kernel.  A Lanczos segment replayed
+ * from a captured graph adds the launches it recorded.  reset != 0 zeroes them. */
+int syk_matvec_launches(int64_t* rows, int64_t* tiled, int64_t* coset, int reset);
+
 /* syk_profile_enable / syk_profile_read -- CUDA-event timing of every apply_H
  * launch the library makes (on the stream it is launched on).  While enabled,
  * each launch is bracketed by two events; elapsed times are accumulated when

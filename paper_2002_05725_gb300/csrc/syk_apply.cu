@@ -170,6 +170,7 @@ void launch_one(const ApplyParams& p, const void* psi, void* y, int64_t ld, int6
   blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 64);
   k_apply_rows<R, BT><<<(unsigned)blocks, threads, 0, st>>>(p, static_cast<const C*>(psi), static_cast<C*>(y), ld, b0);
   count_launch();
+  count_matvec(kMvRows);
 }
 
 template <typename R>
@@ -469,6 +470,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     k_apply_tiled<R, BT, false><<<(unsigned)ntiles, 1u << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
                                                                      static_cast<C*>(y));
     count_launch();
+    count_matvec(kMvTiled);
     SYK_CUDA_CHECK(cudaGetLastError());
     return SYK_OK;
   }
@@ -487,6 +489,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   SYK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_apply_tiled<R, BT, true>, p, groups, ng, ntb, static_cast<const C*>(psi),
                                     static_cast<C*>(y)));
   count_launch();
+  count_matvec(kMvTiled);
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
 }

@@ -294,6 +294,7 @@ int launch_coset_ntb(const ApplyParams& p, const CosetLayout* L, const void* psi
                                       (const float2*)L->t32, x, out));
   }
   count_launch();
+  count_matvec(kMvCoset);
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
 }

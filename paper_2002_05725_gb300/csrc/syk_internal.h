@@ -124,7 +124,12 @@ void count_launch(int64_t n = 1);
 // While a thread captures a CUDA graph its counts go to thread-local tallies (returned by
 // capture_counts_end) so that every replay can add them.
 void capture_counts_begin();
-void capture_counts_end(int64_t* launches, int64_t* applies);
+void capture_counts_end(int64_t* launches, int64_t* applies, int64_t* kinds);
+// Matvec launches by kernel family (kMvRows: k_apply_rows, kMvTiled: k_apply_tiled, kMvCoset:
+// k_apply_coset), counted like the launches above (a replayed graph adds its recorded ones).
+enum { kMvRows = 0, kMvTiled = 1, kMvCoset = 2, kMvKinds = 3 };
+void count_matvec(int kind);
+void count_matvec_replay(const int64_t* kinds);
 bool prof_enabled();
 uint64_t graph_epoch();  // changes whenever captured graphs may hold stale parameters
 void bump_graph_epoch();

@@ -526,6 +526,7 @@ struct SegKey {
 struct SegGraph {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0, applies = 0;
+  int64_t kinds[kMvKinds] = {};
 };
 struct GraphCache {
   std::map<SegKey, SegGraph> graphs;
@@ -561,7 +562,7 @@ int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int
     SYK_CUDA_CHECK(cudaStreamBeginCapture(t_cache.cap, cudaStreamCaptureModeThreadLocal));
     capture_counts_begin();
     const int rc = eager(t_cache.cap);  // recorded, not executed
-    capture_counts_end(&sg.launches, &sg.applies);
+    capture_counts_end(&sg.launches, &sg.applies, sg.kinds);
     const cudaError_t ec = cudaStreamEndCapture(t_cache.cap, &g);
     if (rc != SYK_OK) {
       if (g) cudaGraphDestroy(g);
@@ -582,6 +583,7 @@ int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int
   SYK_CUDA_CHECK(cudaGraphLaunch(it->second.exec, st));
   count_launch(it->second.launches);
   count_applies(it->second.applies);
+  count_matvec_replay(it->second.kinds);
   return SYK_OK;
 }
 

@@ -14,6 +14,7 @@ namespace {
 std::atomic<int64_t> g_applies{0};
 std::atomic<int64_t> g_bases{0};
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_mv[kMvKinds];
 
 struct Prof {
   std::mutex mtx;
@@ -43,6 +44,7 @@ thread_local cudaEvent_t t_start = nullptr;
 
 thread_local bool t_capturing = false;
 thread_local int64_t t_cap_launches = 0, t_cap_applies = 0;
+thread_local int64_t t_cap_mv[kMvKinds] = {};
 std::atomic<uint64_t> g_epoch{1};
 std::atomic<bool> g_graphs{true};
 
@@ -55,14 +57,23 @@ void count_launch(int64_t n) {
   if (t_capturing) t_cap_launches += n;
   else g_launches += n;
 }
+void count_matvec(int kind) {
+  if (t_capturing) t_cap_mv[kind] += 1;
+  else g_mv[kind] += 1;
+}
+void count_matvec_replay(const int64_t* kinds) {
+  for (int k = 0; k < kMvKinds; ++k) g_mv[k] += kinds[k];
+}
 void capture_counts_begin() {
   t_capturing = true;
   t_cap_launches = t_cap_applies = 0;
+  for (int k = 0; k < kMvKinds; ++k) t_cap_mv[k] = 0;
 }
-void capture_counts_end(int64_t* launches, int64_t* applies) {
+void capture_counts_end(int64_t* launches, int64_t* applies, int64_t* kinds) {
   t_capturing = false;
   *launches = t_cap_launches;
   *applies = t_cap_applies;
+  for (int k = 0; k < kMvKinds; ++k) kinds[k] = t_cap_mv[k];
 }
 uint64_t graph_epoch() { return g_epoch.load(); }
 void bump_graph_epoch() { ++g_epoch; }
@@ -162,6 +173,15 @@ extern "C" int syk_counters(int64_t* h_applies, int64_t* krylov_bases, int64_t* 
     syk::g_bases = 0;
     syk::g_launches = 0;
   }
+  return SYK_OK;
+}
+
+extern "C" int syk_matvec_launches(int64_t* rows, int64_t* tiled, int64_t* coset, int reset) {
+  if (rows) *rows = syk::g_mv[syk::kMvRows].load();
+  if (tiled) *tiled = syk::g_mv[syk::kMvTiled].load();
+  if (coset) *coset = syk::g_mv[syk::kMvCoset].load();
+  if (reset)
+    for (int k = 0; k < syk::kMvKinds; ++k) syk::g_mv[k] = 0;
   return SYK_OK;
 }
 

@@ -75,6 +75,7 @@ def load(build_if_missing: bool = False):
         "syk_autotune_reset": (i32, []),
         "syk_lowest_eigenvalues": (i32, [vp, i32, i32, vp, i32, i32, dbl, vp, vp, vp, vp]),
         "syk_fma_peak": (i32, [i32, i32, vp, vp, vp, vp]),
+        "syk_matvec_launches": (i32, [vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -91,7 +92,8 @@ def exported_symbols():
             "syk_otoc", "syk_last_error", "syk_counters", "syk_profile_enable", "syk_profile_read",
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
-            "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak"]
+            "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak",
+            "syk_matvec_launches"]
 
 
 def _check(rc: int, what: str):
@@ -432,3 +434,11 @@ def syk_fma_peak(bits: int = 32, iters: int = 4096, stream=None):
     _check(L.syk_fma_peak(int(bits), int(iters), ctypes.byref(tf), ctypes.byref(sms), ctypes.byref(ms),
                           _stream(stream)), "syk_fma_peak")
     return {"tflops": tf.value, "sms": sms.value, "ms": ms.value}
+
+
+def syk_matvec_launches(reset: bool = False):
+    """Matvec launches by kernel family since the last reset: {"rows", "tiled", "coset"}."""
+    L = load()
+    v = [ctypes.c_int64(0) for _ in range(3)]
+    _check(L.syk_matvec_launches(*(ctypes.byref(x) for x in v), int(bool(reset))), "syk_matvec_launches")
+    return {"rows": v[0].value, "tiled": v[1].value, "coset": v[2].value}

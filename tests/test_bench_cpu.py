@@ -3,6 +3,7 @@ import hashlib
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -18,7 +19,7 @@ def test_time_grid_and_throughput():
 
 
 def test_fp32_peak_from_unit_counts():
-    assert bench.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    assert bench.fp32_peak_tflops(2070.0, 152) == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
 
 
 def test_matvec_kernel_names():
@@ -52,3 +53,13 @@ def test_ncu_summary_parsing_follows_the_source_hash(tmp_path, monkeypatch):
 
 def test_applies_model_is_calibrated():
     assert bench.applies_model(40, 10.0, bench.time_grid(10, 12.0)[1:]) == 808
+
+
+def test_curve_error_is_per_state_max_t_norm():
+    """max_t |F~ - F~ref| / max_t |F~ref| per state (F~ = F / F(0)), largest over the states."""
+    t = np.linspace(0.0, 1.0, 5)
+    ref = np.stack([np.exp(-t), 2.0 * np.exp(-2 * t)], axis=1)
+    F = ref.copy()
+    F[3, 1] += 2e-3 * 2.0  # state 1: F~ off by 2e-3 at one time, max_t |F~ref| = 1
+    assert bench.curve_error(F, ref) == pytest.approx(2e-3)
+    assert bench.curve_error(3.0 * ref, ref) == pytest.approx(0.0, abs=1e-15)  # scale cancels in F~

@@ -44,29 +44,71 @@ def test_G_grad_vs_daleckii_krein(torch, N):
     assert np.abs(db - dbr).max() < 1e-8 * max(np.abs(dJr).max(), np.abs(dbr).max())
 
 
-def test_otoc_grad_N28_finite_differences(torch):
-    """N = 28 (20475 couplings), beta J = 5, t* = 5: central differences (h = 1e-6) of the
-    GPU F~ on sampled couplings and beta, within 1e-4 relative; c64 gradient vs c128."""
-    N, beta, t = 28, 5.0, 5.0
+def _fd_checks(fun, J, beta, dJ, db, rng, ncoup=50, ndir=4, h=1e-6):
+    """Central differences (h = 1e-6) of fun(J, beta) on ncoup sampled couplings, ndir random
+    unit directions in coupling space and beta, against the adjoint gradient (per state)."""
+    sample = rng.choice(len(J), ncoup, replace=False)
+    fdJ, fdb = gr.fd_grad(fun, J, beta, sample, h=h)
+    dirs = rng.standard_normal((ndir, len(J)))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    fdd = np.array([(fun(J + h * d, beta) - fun(J - h * d, beta)) / (2 * h) for d in dirs])
+    scale = np.abs(dJ).max()
+    errs = {"couplings": float(np.abs(dJ[sample] - fdJ).max() / scale),
+            "directions": float(np.abs(dirs @ dJ - fdd).max() / max(np.abs(dirs @ dJ).max(), scale)),
+            "beta": float(np.abs(db - fdb).max() / max(np.abs(db).max(), scale))}
+    return errs
+
+
+@pytest.fixture(scope="module")
+def n28_config():
+    """The gradient workload's own settings: N = 28 (20475 couplings), beta J = 5, t* = 5,
+    Gauss-Legendre sub-intervals of |z| rho <= 0.05 (about 200 time steps), two states."""
+    N = 28
     J = inputs.couplings(N, 0)
-    terms = syk.syk_build_terms(N, J)
-    psi = inputs.random_states(N, 2, 0)
-    dev = to_dev(torch, psi, "c128")
-    F, dJ, db = syk.syk_otoc_grad(terms, beta, 0, 1, t, dev, krylov_dim=40, tol=1e-13, quad_dz=0.25)
+    return {"N": N, "J": J, "terms": syk.syk_build_terms(N, J), "psi": inputs.random_states(N, 2, 0),
+            "beta": 5.0, "t": 5.0, "quad_dz": 0.05}
+
+
+def test_otoc_grad_N28_config_vs_finite_differences(torch, n28_config):
+    """dF~(t*)/dJ and dF~/dbeta (c128) against central differences of the GPU F~ (c128) on 50
+    sampled couplings, 4 random directions and beta, within 1e-4 of the gradient's scale; the
+    c64 gradient against the c128 one within 1e-4."""
+    c = n28_config
+    dev = to_dev(torch, c["psi"], "c128")
+    F, dJ, db = syk.syk_otoc_grad(c["terms"], c["beta"], 0, 1, c["t"], dev, krylov_dim=40, tol=1e-13,
+                                  quad_dz=c["quad_dz"])
 
     def Ftil(Jx, b):
-        tx = syk.syk_build_terms(N, Jx)
-        Fx = syk.syk_otoc(tx, b, 0, 1, [0.0, t], dev, krylov_dim=40, tol=1e-13)
+        Fx = syk.syk_otoc(syk.syk_build_terms(c["N"], Jx), b, 0, 1, [0.0, c["t"]], dev, krylov_dim=40, tol=1e-13)
         return Fx[1] / Fx[0]
 
-    rng = np.random.default_rng(28)
-    sample = rng.choice(len(J), 6, replace=False)
-    fdJ, fdb = gr.fd_grad(Ftil, J, beta, sample, h=1e-6)
-    scale = np.abs(dJ).max()
-    assert np.abs(dJ[sample] - fdJ).max() < 1e-4 * scale
-    assert np.abs(db - fdb).max() < 1e-4 * max(np.abs(db).max(), scale)
-    F64, dJ64, db64 = syk.syk_otoc_grad(terms, beta, 0, 1, t, to_dev(torch, psi, "c64"), krylov_dim=40, tol=1e-7,
-                                        quad_dz=0.25)
+    assert rel(F, Ftil(c["J"], c["beta"])) < 1e-10
+    errs = _fd_checks(Ftil, c["J"], c["beta"], dJ, db, np.random.default_rng(28))
+    assert max(errs.values()) < 1e-4, errs
+    F64, dJ64, db64 = syk.syk_otoc_grad(c["terms"], c["beta"], 0, 1, c["t"], to_dev(torch, c["psi"], "c64"),
+                                        krylov_dim=40, tol=1e-7, quad_dz=c["quad_dz"])
+    assert rel(F64, F) < 1e-5
+    assert rel(dJ64, dJ) < 1e-4
+    assert np.abs(db64 - db).max() < 1e-4 * max(np.abs(db).max(), np.abs(dJ).max())
+
+
+def test_G_grad_N28_config_vs_finite_differences(torch, n28_config):
+    """dG(t*)/dJ and dG/dbeta (G normalised by Z = <phi|phi>) at the same settings."""
+    c = n28_config
+    dev = to_dev(torch, c["psi"], "c128")
+    G, dJ, db = syk.syk_correlator_G_grad(c["terms"], c["beta"], 0, c["t"], dev, krylov_dim=40, tol=1e-13,
+                                          quad_dz=c["quad_dz"])
+
+    def Gt(Jx, b):
+        Gx, _ = syk.syk_correlator_G(syk.syk_build_terms(c["N"], Jx), b, 0, [c["t"]], dev, krylov_dim=40, tol=1e-13)
+        return Gx[0]
+
+    assert rel(G, Gt(c["J"], c["beta"])) < 1e-10
+    errs = _fd_checks(Gt, c["J"], c["beta"], dJ, db, np.random.default_rng(29))
+    assert max(errs.values()) < 1e-4, errs
+    G64, dJ64, db64 = syk.syk_correlator_G_grad(c["terms"], c["beta"], 0, c["t"], to_dev(torch, c["psi"], "c64"),
+                                                krylov_dim=40, tol=1e-7, quad_dz=c["quad_dz"])
+    assert rel(G64, G) < 1e-5
     assert rel(dJ64, dJ) < 1e-4
 
 
