@@ -78,6 +78,18 @@ int syk_term_table(const syk_terms* terms, uint64_t* xmask, uint64_t* zmask, uin
 int syk_apply_H(const syk_terms* terms, int parity, int dtype, const void* psi, void* y,
                 int64_t batch, void* stream);
 
+/* syk_c128_arith -- arithmetic of the complex128 matvec: mode 0 (the default) does the
+ * multiply-adds in double-float form, each double carried as an unevaluated sum of two
+ * floats and every product and sum made exact with FP32 error-free transformations (Knuth's
+ * TwoSum, Dekker's TwoProduct by FMA), because GB300 runs FP64 FMA at 1/64 of the FP32 rate;
+ * mode 1 uses native FP64.  Double-float keeps 48 significand bits, so a matvec differs from
+ * the FP64 one by about 1e-13 relative (FP64 rounding: 1e-16).  Vectors stay complex128 in
+ * memory in both modes; the double-float kernel covers batches of 1, 2, 4, 8 and 16 on the
+ * tiled path (other launches use FP64).  mode < 0 only queries.  Returns the mode in effect
+ * before the call, or SYK_EINVAL.  The paper computes in complex128 throughout; the mode
+ * changes the arithmetic, not the stored precision. */
+int syk_c128_arith(int mode);
+
 /* syk_apply_chi -- y = chi_i psi (Supp. Sec. I.A map, with the 1/sqrt(2) that
  * {chi_i, chi_i} = 1 requires).  psi is in sector parity_in; y is in sector
  * 1 - parity_in.  Device D x batch arrays; must not overlap. */
@@ -97,7 +109,9 @@ int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const double* be
 
 /* syk_workspace_bytes -- device scratch syk_expmv needs for (N, dtype,
  * krylov_dim, batch): the Krylov basis of krylov_dim+1 vectors, one work
- * vector and the FP64 scalars.  `kind` is reserved (pass 0). */
+ * vector and the FP64 scalars, plus for SYK_C128 one more vector (the
+ * double-float copy of the matvec input, see syk_c128_arith).  `kind` is
+ * reserved (pass 0). */
 size_t syk_workspace_bytes(int N, int dtype, int krylov_dim, int64_t batch, int kind);
 
 /* syk_expmv -- out = e^{z H} psi in sector `parity` by Lanczos with full

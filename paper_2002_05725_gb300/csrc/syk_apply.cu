@@ -28,6 +28,7 @@
 // per row, gathers straight from global memory.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <type_traits>
 #include <map>
 #include <mutex>
@@ -71,6 +72,7 @@ struct TileChoice {
   double ms;
   int var = 0;
 };
+static std::atomic<int> g_c128_arith{kC128DoubleFloat};
 static std::mutex g_tune_mtx;
 static std::map<uint64_t, TileChoice> g_tune;
 static uint64_t tune_key(int N, int dtype, int64_t batch) {
@@ -199,8 +201,9 @@ struct TileCfg {
   using C = typename CT<R>::T;
   // rows per thread: more rows share one table-index computation, fewer leave room
   // for more resident warps
-  static constexpr int RPT = sizeof(R) == 4 ? (BT == 1 ? 8 : BT <= 4 ? 4 : BT == 8 ? SYK_RPT_C64_B8 : SYK_RPT_C64_B16)
-                                            : (BT == 1 ? 4 : BT <= 4 ? 2 : 1);
+  static constexpr int RPT = std::is_same<R, float>::value
+                                 ? (BT == 1 ? 8 : BT <= 4 ? 4 : BT == 8 ? SYK_RPT_C64_B8 : SYK_RPT_C64_B16)
+                                 : (BT == 1 ? 4 : BT <= 4 ? 2 : 1);
   static constexpr int ROWB = BT * (int)sizeof(C);
   static constexpr int CH = ROWB >= 16 ? ROWB / 16 : 0;  // 16-byte chunks per row
   static constexpr int NS = CH ? CH : 1;
@@ -217,18 +220,19 @@ struct TileCfg {
 // as clusters that split a tile's mask chunks (otherwise one CTA per tile).
 template <typename R, int BT, bool CL>
 __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* __restrict__ groups, int ngroups,
-                                                     int ntb, const typename CT<R>::T* __restrict__ psi,
-                                                     typename CT<R>::T* __restrict__ y) {
+                                                     int ntb, const void* __restrict__ psi, void* __restrict__ y) {
   using Cfg = TileCfg<R, BT>;
   using C = typename CT<R>::T;
   using S = typename std::conditional<Cfg::CH == 0, C, typename Slot<R>::T>::type;
+  using Out = typename std::conditional<Cfg::CH == 0, C, typename Slot<R>::Out>::type;
+  static_assert(sizeof(Out) == sizeof(S), "output rows have the layout of the staged rows");
   constexpr int RPT = Cfg::RPT, ROWB = Cfg::ROWB, CH = Cfg::CH, NS = Cfg::NS;
   constexpr int GMAX = Cfg::GMAX, TABB = Cfg::TABB;
   const int NT = 1 << ntb, T = RPT << ntb, TILEB = T * ROWB, BUFB = TILEB + Cfg::AUXB;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * BUFB);
-  const C* __restrict__ t4 = static_cast<const C*>(p.m4_tab);
-  const C* __restrict__ t2 = static_cast<const C*>(p.m2_tab);
+  const C* __restrict__ t4 = tab4<R>(p);
+  const C* __restrict__ t2 = tab2<R>(p);
   const int tid = threadIdx.x, lane = tid & 31;
   // the CTAs of a cluster share one tile and split its mask chunks round-robin
   const uint32_t crank = CL ? tma::cluster_rank() : 0u, csize = CL ? tma::cluster_size() : 1u;
@@ -256,15 +260,15 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       else acc[i][k] = Slot<R>::zero();
     }
 
-  // y_row += (cr + i ci) * psi_tile[sr] for this thread's row slot i
-  auto mac_row = [&](S* a, R cr, R ci, const unsigned char* tb, uint32_t sr) {
+  // y_row += c * psi_tile[sr] for this thread's row slot i
+  auto mac_row = [&](S* a, const C c, const unsigned char* tb, uint32_t sr) {
     if constexpr (CH == 0) {
       const C v = reinterpret_cast<const C*>(tb)[sr];
-      cmac(a[0], cr, ci, v);
+      cmac(a[0], c.x, c.y, v);
     } else {
       const unsigned char* row = tb + (size_t)sr * ROWB;
 #pragma unroll
-      for (int k = 0; k < NS; ++k) Slot<R>::mac(a[k], cr, ci, *reinterpret_cast<const S*>(row + soff[k]));
+      for (int k = 0; k < NS; ++k) Slot<R>::mac(a[k], c, *reinterpret_cast<const S*>(row + soff[k]));
     }
   };
 
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
         const uint32_t idx0 = supp_bits(xf[0], rec.z) | ((__popc(rec.y & xf[0]) & 1u) << 4);
         const uint32_t fl = rec.w >> fsh;
         const C* tab = stab + kk * 32;
-        if constexpr (CH == 0 && SYK_SHARED_COEF) {
+        if constexpr (CH == 0 && SYK_SHARED_COEF && std::is_same<R, float>::value) {
           // one-state rows (8 bytes): the table lookup costs as much shared-memory traffic as
           // the row itself.  When no row-slot bit of this thread touches the mask's support
           // (flip bits 0..3 of every row bit clear; the same for the whole warp), every row
@@ -326,9 +330,9 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
               if (i & 2) sg ^= fl << 22;
               if (i & 4) sg ^= fl << 17;
               sg &= 0x80000000u;  // flip bit 4 of the row bits' groups, moved to the sign bit
-              const R cr = __int_as_float(__float_as_int(cf.x) ^ (int)sg);
-              const R ci = __int_as_float(__float_as_int(cf.y) ^ (int)sg);
-              mac_row(acc[i], cr, ci, tb, (uint32_t)(tid + i * NT) ^ lo);
+              const float cr = __int_as_float(__float_as_int(cf.x) ^ (int)sg);
+              const float ci = __int_as_float(__float_as_int(cf.y) ^ (int)sg);
+              mac_row(acc[i], make_float2(cr, ci), tb, (uint32_t)(tid + i * NT) ^ lo);
             }
             continue;
           }
@@ -339,8 +343,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
           if (i & 1) idx ^= fl & 31u;
           if (i & 2) idx ^= (fl >> 5) & 31u;
           if (i & 4) idx ^= (fl >> 10) & 31u;
-          const C cf = tab[idx];
-          mac_row(acc[i], cf.x, cf.y, tb, (uint32_t)(tid + i * NT) ^ lo);
+          mac_row(acc[i], tab[idx], tb, (uint32_t)(tid + i * NT) ^ lo);
         }
       }
       // popcount-2 masks
@@ -349,17 +352,18 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
         const uint4 rec = __ldg(&p.m2_rec[k]);
         const uint32_t lo = rec.x & (uint32_t)(T - 1);
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-          R cr, ci;
-          pc2_coef<C, R>(t2, k, n, rec, xf[i], cr, ci);
-          mac_row(acc[i], cr, ci, tb, (uint32_t)(tid + i * NT) ^ lo);
-        }
+        for (int i = 0; i < RPT; ++i) mac_row(acc[i], pc2_c<R>(t2, k, n, rec, xf[i]), tb, (uint32_t)(tid + i * NT) ^ lo);
       }
       // diagonal (the own tile: first chunk of h = 0)
       if ((uint32_t)gr.x == 0x80000000u) {
 #pragma unroll
+        for (int i = 0; i < RPT; ++i) mac_row(acc[i], diag_c<R>(p, n, xf[i]), tb, (uint32_t)(tid + i * NT));
+      }
+      if constexpr (CH != 0) {  // double-float accumulators: renormalise once per chunk
+#pragma unroll
         for (int i = 0; i < RPT; ++i)
-          mac_row(acc[i], diag_coef<R>(static_cast<const R*>(p.wd), n, xf[i]), R(0), tb, (uint32_t)(tid + i * NT));
+#pragma unroll
+          for (int k = 0; k < NS; ++k) Slot<R>::renorm(acc[i][k]);
       }
     }
     // every thread is done with buffer g&1 before it is refilled; agree on failure
@@ -387,13 +391,13 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     } else {
       unsigned char* out = dst + row * ROWB;
 #pragma unroll
-      for (int k = 0; k < NS; ++k) *reinterpret_cast<S*>(out + soff[k]) = acc[i][k];
+      for (int k = 0; k < NS; ++k) *reinterpret_cast<Out*>(out + soff[k]) = Slot<R>::out(acc[i][k]);
     }
   }
   if constexpr (CL) {
     // every CTA of the cluster reduces 1/csize of the tile's rows over the partial sums
     // held in the cluster's shared memories (fixed rank order: deterministic)
-    using V16 = typename Slot<R>::T;
+    using V16 = typename Slot<R>::Out;
     tma::cluster_sync();
     const int units = TILEB / 16 / (int)csize;
     const uint32_t base = tma::saddr(sm) + crank * (uint32_t)units * 16u;
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
       V16 sum = tma::ld_cluster(tma::map_rank(base + 16u * u, 0), V16{});
       for (uint32_t r = 1; r < csize; ++r) {
         const V16 v = tma::ld_cluster(tma::map_rank(base + 16u * u, r), V16{});
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (std::is_same<V16, float4>::value) {
           sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
         } else {
           sum.x += v.x; sum.y += v.y;
@@ -417,11 +421,10 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
 template <typename R, int BT>
 int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st) {
   using Cfg = TileCfg<R, BT>;
-  using C = typename CT<R>::T;
   int ntb = 8, cs = 1;
   TileChoice tc;
-  const bool tuned = tile_choice_lookup(p.n * 2, sizeof(R) == 4 ? SYK_C64 : SYK_C128, BT, &tc);
-  if constexpr (sizeof(R) == 4 && (BT == 4 || BT == 8 || BT == 16)) {
+  const bool tuned = tile_choice_lookup(p.n * 2, std::is_same<R, float>::value ? SYK_C64 : SYK_C128, BT, &tc);
+  if constexpr (std::is_same<R, float>::value && (BT == 4 || BT == 8 || BT == 16)) {
     if (tuned && tc.var > 0) {
       const int rc = launch_coset_var(p, BT, psi, y, st, tc.var, tc.ntb, tc.cs);
       if (rc <= 0) return rc;  // launched or failed; 1: not applicable, plain tiles below
@@ -467,8 +470,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   SYK_TRY(ensure_smem_limit((const void*)k_apply_tiled<R, BT, false>, (int)Cfg::smem(Cfg::RPT << 8)));
   SYK_TRY(ensure_smem_limit((const void*)k_apply_tiled<R, BT, true>, (int)Cfg::smem(Cfg::RPT << 8)));
   if (cs == 1) {
-    k_apply_tiled<R, BT, false><<<(unsigned)ntiles, 1u << ntb, smem, st>>>(p, groups, ng, ntb, static_cast<const C*>(psi),
-                                                                     static_cast<C*>(y));
+    k_apply_tiled<R, BT, false><<<(unsigned)ntiles, 1u << ntb, smem, st>>>(p, groups, ng, ntb, psi, y);
     count_launch();
     count_matvec(kMvTiled);
     SYK_CUDA_CHECK(cudaGetLastError());
@@ -486,8 +488,7 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  SYK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_apply_tiled<R, BT, true>, p, groups, ng, ntb, static_cast<const C*>(psi),
-                                    static_cast<C*>(y)));
+  SYK_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_apply_tiled<R, BT, true>, p, groups, ng, ntb, psi, y));
   count_launch();
   count_matvec(kMvTiled);
   SYK_CUDA_CHECK(cudaGetLastError());
@@ -538,12 +539,59 @@ __global__ void k_apply_chi(int n, int maj, int sector_out, int64_t D, int64_t b
   }
 }
 
+// Double-float copy of a complex128 vector: element e becomes (re_hi, im_hi, re_lo, im_lo)
+// with hi = fl32(d) and lo = fl32(d - hi).
+__global__ void k_split_df(const double2* __restrict__ x, float4* __restrict__ out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[e];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    const float rl = __double2float_rn(__dsub_rn(v.x, (double)rh));
+    const float il = __double2float_rn(__dsub_rn(v.y, (double)ih));
+    out[e] = make_float4(rh, ih, rl, il);
+  }
+}
+
+// complex128 matvec in double-float arithmetic on the tiled kernel (batches of 1, 2, 4, 8, 16):
+// the input is first split into its double-float copy (p.df_split, or a buffer allocated on
+// the stream for this call); returns 1 if the tiled kernel does not apply to this launch.
+int launch_apply_df(const ApplyParams& p, const void* psi, void* y, int64_t batch, cudaStream_t st) {
+  if (batch != 1 && batch != 2 && batch != 4 && batch != 8 && batch != 16) return 1;
+  if ((reinterpret_cast<uintptr_t>(y) & 15) || p.D < 64) return 1;
+  const size_t need = size_t(p.D) * batch * sizeof(float4);
+  void* split = p.df_split;
+  bool owned = false;
+  if (!split || p.df_split_bytes < need) {
+    if (p.no_alloc) return 1;
+    SYK_CUDA_CHECK(cudaMallocAsync(&split, need, st));
+    owned = true;
+  }
+  const int64_t n = p.D * batch;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, (int64_t)sm_count() * 16);
+  k_split_df<<<(unsigned)blocks, threads, 0, st>>>(static_cast<const double2*>(psi), static_cast<float4*>(split), n);
+  count_launch();
+  int rc;
+  switch (batch) {
+    case 1: rc = launch_tiled<DF, 1>(p, split, y, st); break;
+    case 2: rc = launch_tiled<DF, 2>(p, split, y, st); break;
+    case 4: rc = launch_tiled<DF, 4>(p, split, y, st); break;
+    case 8: rc = launch_tiled<DF, 8>(p, split, y, st); break;
+    default: rc = launch_tiled<DF, 16>(p, split, y, st); break;
+  }
+  if (owned) cudaFreeAsync(split, st);
+  return rc;
+}
+
 }  // namespace
+
+int c128_arith() { return g_c128_arith.load(); }
 
 int launch_apply_H(const ApplyParams& p, int dtype, const void* psi, void* y, int64_t batch, cudaStream_t st) {
   prof_before_apply(st);
-  int rc = dtype == SYK_C64 ? launch_apply_T<float>(p, psi, y, batch, st)
-                            : launch_apply_T<double>(p, psi, y, batch, st);
+  int rc = 1;
+  if (dtype == SYK_C128 && c128_arith() == kC128DoubleFloat) rc = launch_apply_df(p, psi, y, batch, st);
+  if (rc > 0)
+    rc = dtype == SYK_C64 ? launch_apply_T<float>(p, psi, y, batch, st) : launch_apply_T<double>(p, psi, y, batch, st);
   prof_after_apply(st);
   count_applies(batch);
   return rc;
@@ -578,6 +626,19 @@ extern "C" int syk_apply_H(const syk_terms* terms, int parity, int dtype, const 
   syk::ApplyParams p;
   SYK_TRY(syk::make_apply_params(terms, parity, dtype, &p));
   return syk::launch_apply_H(p, dtype, psi, y, batch, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int syk_c128_arith(int mode) {
+  syk::clear_error();
+  const int prev = syk::g_c128_arith.load();
+  if (mode < 0) return prev;
+  if (mode != syk::kC128DoubleFloat && mode != syk::kC128Fp64) {
+    syk::set_error("syk_c128_arith: mode must be 0 (double-float) or 1 (FP64), got %d", mode);
+    return SYK_EINVAL;
+  }
+  syk::g_c128_arith = mode;
+  syk::bump_graph_epoch();  // captured matvec launches carry the other kernel
+  return prev;
 }
 
 extern "C" int syk_apply_chi(int N, int i, int parity_in, int dtype, const void* psi, void* y, int64_t batch,
@@ -618,6 +679,17 @@ extern "C" int syk_autotune_apply(const syk_terms* terms, int parity, int dtype,
     return SYK_ENOMEM;
   }
   cudaMemsetAsync(x, 0, vb, st);
+  void* split = nullptr;  // double-float copy of the input (complex128)
+  if (dtype == SYK_C128) {
+    if (cudaMallocAsync(&split, vb, st) != cudaSuccess) {
+      cudaFreeAsync(x, st);
+      cudaFreeAsync(y, st);
+      set_error("syk_autotune_apply: cannot allocate %zu bytes", vb);
+      return SYK_ENOMEM;
+    }
+    P.df_split = split;
+    P.df_split_bytes = vb;
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -651,6 +723,7 @@ extern "C" int syk_autotune_apply(const syk_terms* terms, int parity, int dtype,
   cudaEventDestroy(e1);
   cudaFreeAsync(x, st);
   cudaFreeAsync(y, st);
+  if (split) cudaFreeAsync(split, st);
   if (rc != SYK_OK || best.ntb == 0) {
     std::lock_guard<std::mutex> lk(g_tune_mtx);
     g_tune.erase(tune_key(N, dtype, batch));

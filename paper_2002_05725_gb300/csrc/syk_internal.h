@@ -42,6 +42,11 @@ struct DeviceTables {
   float2* m2_t32 = nullptr;
   double* wd64 = nullptr;     // n x n upper triangle: diagonal couplings w_cd
   float* wd32 = nullptr;
+  // double-float copies of the FP64 tables for the complex128 matvec: every double d is
+  // stored as floats (hi, lo) = (fl(d), fl(d - hi)); complex entries as (re_hi, im_hi, re_lo, im_lo)
+  float4* m4_tdf = nullptr;
+  float4* m2_tdf = nullptr;
+  float2* wd_df = nullptr;
   int* status = nullptr;      // device status word of the matvec (bounded-wait timeouts)
 };
 
@@ -57,8 +62,13 @@ struct ApplyParams {
   const void* m2_tab;
   const void* wd;
   int* status;
+  const float4* m4_tdf;    // double-float tables (complex128 matvec in FP32 arithmetic)
+  const float4* m2_tdf;
+  const float2* wd_df;
   const syk_terms* terms;  // host-side: tile-group lists
   bool no_alloc;           // host-side: never allocate (use only cached tile-group lists)
+  void* df_split;          // host-side: device buffer (>= D x batch x 16 bytes) for the split
+  size_t df_split_bytes;   // copy of a complex128 input, or NULL (then allocated per call)
 };
 
 // Chunks of X-masks sharing the compact-mask bits h above a tile of 2^tb rows, at
@@ -134,6 +144,11 @@ bool prof_enabled();
 uint64_t graph_epoch();  // changes whenever captured graphs may hold stale parameters
 void bump_graph_epoch();
 bool graphs_enabled();
+
+// Arithmetic of the complex128 matvec: double-float (FP32 error-free transformations, the
+// default) or native FP64 (syk_c128_arith).
+enum { kC128DoubleFloat = 0, kC128Fp64 = 1 };
+int c128_arith();
 
 // Raises func's dynamic shared-memory limit to at least `bytes` on the current device (the
 // attribute is per device; done once per kernel and device, thread-safe).

@@ -445,6 +445,7 @@ size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B) {
   s += align_up(sizeof(double));                      // sacc
   s += align_up(sizeof(double2) * m * B);             // c
   s += align_up(sizeof(int) * 4);                     // status
+  if (dtype == SYK_C128) s += align_up(size_t(D) * B * 16);  // split
   return s;
 }
 
@@ -486,6 +487,7 @@ int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype
   ws->sacc = (double*)take(sizeof(double));
   ws->c = (double2*)take(sizeof(double2) * m * B);
   ws->status = (int*)take(sizeof(int) * 4);
+  ws->split = dtype == SYK_C128 ? take(size_t(D) * B * 16) : nullptr;
   return SYK_OK;
 }
 
@@ -591,8 +593,9 @@ int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int
 // into Krylov bases as the error estimate allows, and each output is combined from the basis
 // whose step covers its fraction.  Restarts pass through outs[nf-1], written last.
 template <typename R>
-int expmv_T(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, const double* fr, int nf,
+int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const void* psi, const double* fr, int nf,
             void* const* outs, double tol, KrylovWS& ws, cudaStream_t st, int* nsteps) {
+  const ApplyParams P = ws.with_split(P_in);
   const int64_t B = ws.B;
   const size_t vs = size_t(ws.D) * B;
   const int m = ws.m;
@@ -768,7 +771,8 @@ int expmv_points(const ApplyParams& P, int dtype, std::complex<double> z, const 
 
 namespace {
 template <typename R>
-int lanczos_steps_T(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st) {
+int lanczos_steps_T(const ApplyParams& P_in, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st) {
+  const ApplyParams P = ws.with_split(P_in);
   const size_t vs = size_t(ws.D) * ws.B;
   const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
   for (int j = j0; j < j1; ++j) {

@@ -30,9 +30,19 @@ struct KrylovWS {
   double* sacc = nullptr;    // 1
   double2* c = nullptr;      // m * B
   int* status = nullptr;     // 4 ints
+  char* split = nullptr;     // complex128 only: double-float copy of the matvec input (D*B float4)
   void* host_stage = nullptr;  // host buffer (>= 64 B) for status reads; NULL: pinned scratch
   size_t vec_bytes() const { return size_t(D) * B * dtype_size(dtype); }
   char* vec(int k) const { return V + size_t(k) * vec_bytes(); }
+  // the matvec parameters with this workspace's split buffer (complex128 in double-float)
+  ApplyParams with_split(const ApplyParams& P) const {
+    ApplyParams q = P;
+    if (split) {
+      q.df_split = split;
+      q.df_split_bytes = size_t(D) * B * 16;
+    }
+    return q;
+  }
 };
 
 size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B);

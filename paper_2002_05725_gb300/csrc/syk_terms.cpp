@@ -276,7 +276,8 @@ extern "C" void syk_free_terms(syk_terms* t) {
     cudaGetDevice(&prev);
     cudaSetDevice(t->dev.device);
     void* ptrs[] = {t->dev.m4_rec, t->dev.m4_t64, t->dev.m4_t32, t->dev.m2_rec, t->dev.m2_t64,
-                    t->dev.m2_t32, t->dev.wd64,   t->dev.wd32,   t->dev.status};
+                    t->dev.m2_t32, t->dev.wd64,   t->dev.wd32,   t->dev.status,
+                    t->dev.m4_tdf, t->dev.m2_tdf, t->dev.wd_df};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (auto& kv : t->groups_dev)
@@ -351,6 +352,26 @@ int ensure_device_tables(const syk_terms* t) {
   SYK_TRY(upload(&d.m2_t32, f2.data(), f2.size() * 4));
   SYK_TRY(upload(&d.wd64, t->wdiag.data(), t->wdiag.size() * 8));
   SYK_TRY(upload(&d.wd32, fd.data(), fd.size() * 4));
+  // double-float copies: each double d as (hi, lo) = (fl(d), fl(d - hi)); complex tables
+  // interleave (re_hi, im_hi, re_lo, im_lo)
+  auto split = [](double v, float* hi, float* lo) {
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
+  };
+  auto split_complex = [&](const std::vector<double>& src) {
+    std::vector<float> out(src.size() * 2);
+    for (size_t e = 0; e < src.size() / 2; ++e) {
+      split(src[2 * e], &out[4 * e], &out[4 * e + 2]);
+      split(src[2 * e + 1], &out[4 * e + 1], &out[4 * e + 3]);
+    }
+    return out;
+  };
+  const std::vector<float> d4 = split_complex(t->m4_tab), d2 = split_complex(t->m2_tab);
+  std::vector<float> dd(t->wdiag.size() * 2);
+  for (size_t e = 0; e < t->wdiag.size(); ++e) split(t->wdiag[e], &dd[2 * e], &dd[2 * e + 1]);
+  SYK_TRY(upload(&d.m4_tdf, d4.data(), d4.size() * 4));
+  SYK_TRY(upload(&d.m2_tdf, d2.data(), d2.size() * 4));
+  SYK_TRY(upload(&d.wd_df, dd.data(), dd.size() * 4));
   SYK_TRY(upload(&d.status, nullptr, 16));
   SYK_CUDA_CHECK(cudaMemset(d.status, 0, 16));
   d.device = cur;
@@ -383,8 +404,13 @@ int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p)
   p->m2_tab = f ? (const void*)t->dev.m2_t32 : (const void*)t->dev.m2_t64;
   p->wd = f ? (const void*)t->dev.wd32 : (const void*)t->dev.wd64;
   p->status = t->dev.status;
+  p->m4_tdf = t->dev.m4_tdf;
+  p->m2_tdf = t->dev.m2_tdf;
+  p->wd_df = t->dev.wd_df;
   p->terms = t;
   p->no_alloc = false;
+  p->df_split = nullptr;
+  p->df_split_bytes = 0;
   return SYK_OK;
 }
 

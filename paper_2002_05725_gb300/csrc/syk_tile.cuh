@@ -5,8 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "syk_cplx.cuh"
+#include "syk_df.cuh"
 #include "syk_internal.h"
 
 namespace syk {
@@ -89,25 +91,56 @@ __device__ __forceinline__ double2 ld_cluster(uint32_t a, double2) {
 }
 }  // namespace tma
 
+// 16-byte chunk of a row: T is the chunk (and accumulator) type, Out what the output row
+// stores, mac adds coefficient x chunk, renorm is called after every mask chunk.
 template <typename R>
-struct Slot;  // 16-byte chunk of a row
+struct Slot;
 template <>
 struct Slot<float> {
   using T = float4;  // two complex64
+  using Out = float4;
   static __device__ __forceinline__ void mac(float4& a, float cr, float ci, const float4 v) {
     a.x = fmaf(cr, v.x, fmaf(-ci, v.y, a.x));
     a.y = fmaf(cr, v.y, fmaf(ci, v.x, a.y));
     a.z = fmaf(cr, v.z, fmaf(-ci, v.w, a.z));
     a.w = fmaf(cr, v.w, fmaf(ci, v.z, a.w));
   }
+  static __device__ __forceinline__ void mac(float4& a, const float2 c, const float4 v) { mac(a, c.x, c.y, v); }
   static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ Out out(const float4 a) { return a; }
+  static __device__ __forceinline__ void renorm(float4&) {}
 };
 template <>
 struct Slot<double> {
   using T = double2;  // one complex128
+  using Out = double2;
   static __device__ __forceinline__ void mac(double2& a, double cr, double ci, const double2 v) { cmac(a, cr, ci, v); }
+  static __device__ __forceinline__ void mac(double2& a, const double2 c, const double2 v) { cmac(a, c.x, c.y, v); }
   static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ Out out(const double2 a) { return a; }
+  static __device__ __forceinline__ void renorm(double2&) {}
 };
+template <>
+struct Slot<DF> {
+  using T = float4;  // one complex128 as a double-float pair
+  using Out = double2;
+  static __device__ __forceinline__ void mac(float4& a, const float4 c, const float4 v) { df_cmac(a, c, v); }
+  static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ Out out(const float4 a) { return df_to_double2(a); }
+  static __device__ __forceinline__ void renorm(float4& a) { df_renorm4(a); }
+};
+
+// Table pointers of a launch for arithmetic R (the double-float kernel reads the split tables).
+template <typename R>
+__device__ __forceinline__ const typename CT<R>::T* tab4(const ApplyParams& p) {
+  if constexpr (std::is_same<R, DF>::value) return p.m4_tdf;
+  else return static_cast<const typename CT<R>::T*>(p.m4_tab);
+}
+template <typename R>
+__device__ __forceinline__ const typename CT<R>::T* tab2(const ApplyParams& p) {
+  if constexpr (std::is_same<R, DF>::value) return p.m2_tdf;
+  else return static_cast<const typename CT<R>::T*>(p.m2_tab);
+}
 
 // diagonal coefficient c_0(x) = sum_{c<d} w_cd (-1)^{x_c + x_d}
 template <typename R>
@@ -122,6 +155,24 @@ __device__ __forceinline__ R diag_coef(const R* __restrict__ wd, int n, uint32_t
     dsum += ((xf >> c) & 1u) ? -inner : inner;
   }
   return dsum;
+}
+
+// the diagonal coefficient as a complex value of the kernel's coefficient type
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T diag_c(const ApplyParams& p, int n, uint32_t xf) {
+  if constexpr (std::is_same<R, DF>::value) {
+    // sum_{c<d} w_cd (-1)^{x_c + x_d} in double-float (w_cd stored as (hi, lo))
+    float hi = 0.f, lo = 0.f;
+    for (int c = 0; c < n - 1; ++c)
+      for (int d = c + 1; d < n; ++d) {
+        const float2 w = __ldg(&p.wd_df[c * n + d]);
+        df_add_signed(hi, lo, w.x, w.y, ((xf >> c) ^ (xf >> d)) & 1u);
+      }
+    df_renorm(hi, lo);
+    return make_float4(hi, 0.f, lo, 0.f);
+  } else {
+    return make_c<R>(diag_coef<R>(static_cast<const R*>(p.wd), n, xf), R(0));
+  }
 }
 
 // popcount-2 coefficient c_m(x) = (-1)^{popcount(zeta_f & x)} sum_c (-1)^{x_c} W_c[u(x)]
@@ -149,5 +200,31 @@ __device__ __forceinline__ void pc2_coef(const C* __restrict__ t2, int k, int n,
   }
 }
 
+
+// the popcount-2 coefficient as a complex value of the kernel's coefficient type
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T pc2_c(const typename CT<R>::T* __restrict__ t2, int k, int n, uint4 rec,
+                                                  uint32_t xf) {
+  if constexpr (std::is_same<R, DF>::value) {
+    const uint32_t a = rec.z & 0xffu, bb = (rec.z >> 8) & 0xffu;
+    const uint32_t u = ((xf >> a) & 1u) | (((xf >> bb) & 1u) << 1);
+    const float4* W = t2 + (size_t)k * n * 4 + u;
+    const bool flip = __popc(rec.y & xf) & 1;
+    float rh = 0.f, ih = 0.f, rl = 0.f, il = 0.f;
+    for (int c = 0; c < n; ++c) {
+      const float4 w = __ldg(&W[4 * c]);
+      const bool neg = (((xf >> c) & 1u) != 0u) != flip;
+      df_add_signed(rh, rl, w.x, w.z, neg);
+      df_add_signed(ih, il, w.y, w.w, neg);
+    }
+    df_renorm(rh, rl);
+    df_renorm(ih, il);
+    return make_float4(rh, ih, rl, il);
+  } else {
+    typename CT<R>::T c;
+    pc2_coef<typename CT<R>::T, R>(t2, k, n, rec, xf, c.x, c.y);
+    return c;
+  }
+}
 
 }  // namespace syk

@@ -31,9 +31,12 @@ def main():
     ap.add_argument("--tile", default=None,
                     help="force the launch shape 'ntb,cluster[,variant]' (no tuning sweep; variant 0 = k_apply_tiled, "
                          "1..3 = k_apply_coset with 2^variant rows per thread)")
+    ap.add_argument("--c128-arith", default="df", choices=["df", "fp64"],
+                    help="complex128 matvec arithmetic: double-float (default) or native FP64")
     a = ap.parse_args()
     import torch
     syk.load()
+    syk.syk_c128_arith(syk.C128_DOUBLE_FLOAT if a.c128_arith == "df" else syk.C128_FP64)
     dt = torch.complex64 if a.dtype == "c64" else torch.complex128
     terms = syk.syk_build_terms(a.N, inputs.couplings(a.N, 0))
     psi = inputs.random_states_device(a.N, a.batch, 1, "cuda", dt)
@@ -61,7 +64,7 @@ def main():
     ms = e0.elapsed_time(e1) / a.reps
     nnz = terms.D * terms.nmasks
     s = 8 if a.dtype == "c64" else 16
-    out = {"N": a.N, "batch": a.batch, "dtype": a.dtype, "ms_per_apply": ms,
+    out = {"N": a.N, "batch": a.batch, "dtype": a.dtype, "c128_arith": a.c128_arith, "ms_per_apply": ms,
            "tflops": 8.0 * nnz * a.batch / (ms * 1e-3) / 1e12,
            "gather_GBps": nnz * a.batch * s / (ms * 1e-3) / 1e9, "nnz": nnz, "tile": tile}
     if a.expmv is not None:

@@ -76,6 +76,7 @@ def load(build_if_missing: bool = False):
         "syk_lowest_eigenvalues": (i32, [vp, i32, i32, vp, i32, i32, dbl, vp, vp, vp, vp]),
         "syk_fma_peak": (i32, [i32, i32, vp, vp, vp, vp]),
         "syk_matvec_launches": (i32, [vp, vp, vp, i32]),
+        "syk_c128_arith": (i32, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -93,7 +94,7 @@ def exported_symbols():
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
             "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak",
-            "syk_matvec_launches"]
+            "syk_matvec_launches", "syk_c128_arith"]
 
 
 def _check(rc: int, what: str):
@@ -442,3 +443,15 @@ def syk_matvec_launches(reset: bool = False):
     v = [ctypes.c_int64(0) for _ in range(3)]
     _check(L.syk_matvec_launches(*(ctypes.byref(x) for x in v), int(bool(reset))), "syk_matvec_launches")
     return {"rows": v[0].value, "tiled": v[1].value, "coset": v[2].value}
+
+
+C128_DOUBLE_FLOAT, C128_FP64 = 0, 1
+
+
+def syk_c128_arith(mode: int = -1) -> int:
+    """Sets the complex128 matvec arithmetic (0: double-float, 1: FP64; < 0 only queries) and
+    returns the previous mode."""
+    rc = load().syk_c128_arith(int(mode))
+    if rc < 0:
+        _check(rc, "syk_c128_arith")
+    return rc
