@@ -78,6 +78,15 @@ int syk_term_table(const syk_terms* terms, uint64_t* xmask, uint64_t* zmask, uin
 int syk_apply_H(const syk_terms* terms, int parity, int dtype, const void* psi, void* y,
                 int64_t batch, void* stream);
 
+/* syk_status -- synchronises `stream` and reads the status word that the matvec kernels
+ * launched with this term set (on the current device) write when a bounded device-side wait
+ * gives up: SYK_ETIMEOUT if a wait for a staged tile ran out since the last reset (those
+ * results are incomplete; the kernel still let every copy it had started land before it
+ * exited, so the context stays usable), else SYK_OK.  syk_apply_H itself is asynchronous
+ * and cannot report it; syk_expmv and the correlators check the word at every convergence
+ * check and return SYK_ETIMEOUT.  The word is sticky: reset != 0 clears it. */
+int syk_status(const syk_terms* terms, int reset, void* stream);
+
 /* syk_c128_arith -- arithmetic of the complex128 matvec: mode 0 (the default) does the
  * multiply-adds in double-float form, each double carried as an unevaluated sum of two
  * floats and every product and sum made exact with FP32 error-free transformations (Knuth's

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   int g = 0;  // index among this CTA's chunks
   for (; g < nmine; ++g) {
     if (g + 1 < nmine) issue(g + 1);
-    const bool ok = tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
+    const bool ok = tma::wait_bounded(&bar[g & 1], (g >> 1) & 1, tma::kWaitPolls);
     const int4 gr = __ldg(&groups[(int)crank + g * (int)csize]);
     const unsigned char* tb = sm + (g & 1) * BUFB;
     if (ok) {
@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     // drain: let any copy still in flight land before the buffers are reused or the CTA exits
     if (tid == 0) {
       atomicOr(p.status, 4);
-      tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
-      if (g + 1 < nmine) tma::wait_bounded(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
+      tma::wait_bounded(&bar[g & 1], (g >> 1) & 1, tma::kDrainPolls);
+      if (g + 1 < nmine) tma::wait_bounded(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1, tma::kDrainPolls);
     }
     __syncthreads();
   }
@@ -626,6 +626,27 @@ extern "C" int syk_apply_H(const syk_terms* terms, int parity, int dtype, const 
   syk::ApplyParams p;
   SYK_TRY(syk::make_apply_params(terms, parity, dtype, &p));
   return syk::launch_apply_H(p, dtype, psi, y, batch, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int syk_status(const syk_terms* terms, int reset, void* stream) {
+  syk::clear_error();
+  if (!terms) {
+    syk::set_error("syk_status: NULL terms");
+    return SYK_EINVAL;
+  }
+  int cur = -1;
+  SYK_CUDA_CHECK(cudaGetDevice(&cur));
+  if (terms->dev.device != cur || !terms->dev.status) return SYK_OK;  // nothing launched on this device
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int word = 0;
+  SYK_CUDA_CHECK(cudaMemcpyAsync(&word, terms->dev.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (reset) SYK_CUDA_CHECK(cudaMemsetAsync(terms->dev.status, 0, sizeof(int), st));
+  if (word & 4) {
+    syk::set_error("syk_status: a bounded wait of a matvec for a staged tile gave up (its result is incomplete)");
+    return SYK_ETIMEOUT;
+  }
+  return SYK_OK;
 }
 
 extern "C" int syk_c128_arith(int mode) {

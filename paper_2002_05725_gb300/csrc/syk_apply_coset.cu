@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(1 << NTB) k_apply_coset(ApplyParams p, const i
   int g = 0;
   for (; g < nmine; ++g) {
     if (g + 1 < nmine) issue(g + 1);
-    const bool ok = tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
+    const bool ok = tma::wait_bounded(&bar[g & 1], (g >> 1) & 1, tma::kWaitPolls);
     const int c = (int)crank + g * (int)csize;
     const int4 gr = __ldg(&chunks[c]);
     const unsigned char* tb = sm + (g & 1) * BUFB;
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(1 << NTB) k_apply_coset(ApplyParams p, const i
   if (failed) {
     if (tid == 0) {
       atomicOr(p.status, 4);
-      tma::wait_bounded(&bar[g & 1], (g >> 1) & 1);
-      if (g + 1 < nmine) tma::wait_bounded(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1);
+      tma::wait_bounded(&bar[g & 1], (g >> 1) & 1, tma::kDrainPolls);
+      if (g + 1 < nmine) tma::wait_bounded(&bar[(g + 1) & 1], ((g + 1) >> 1) & 1, tma::kDrainPolls);
     }
     __syncthreads();
   }

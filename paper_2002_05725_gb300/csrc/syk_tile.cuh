@@ -50,12 +50,21 @@ __device__ __forceinline__ bool try_wait(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for phase `parity` of b; gives up after a bounded number of polls.
-__device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
+// Waits for phase `parity` of b; gives up after `polls` polls (each try_wait may itself block
+// for a short hardware-defined time).
+__device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity, uint32_t polls) {
+  for (uint32_t it = 0; it < polls; ++it)
     if (try_wait(b, parity)) return true;
   return false;
 }
+// Poll budget of the main-loop waits for staged tiles (a build-time knob: a build with 0 makes
+// every such wait give up at once, which exercises the timeout path), and of the drain that
+// lets in-flight copies land before a CTA that gave up exits (always the full budget).
+#ifndef SYK_WAIT_POLLS
+#define SYK_WAIT_POLLS (1u << 22)
+#endif
+constexpr uint32_t kWaitPolls = SYK_WAIT_POLLS;
+constexpr uint32_t kDrainPolls = 1u << 22;
 // thread-block cluster helpers
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;

@@ -77,6 +77,7 @@ def load(build_if_missing: bool = False):
         "syk_fma_peak": (i32, [i32, i32, vp, vp, vp, vp]),
         "syk_matvec_launches": (i32, [vp, vp, vp, i32]),
         "syk_c128_arith": (i32, [i32]),
+        "syk_status": (i32, [vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -94,7 +95,7 @@ def exported_symbols():
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
             "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak",
-            "syk_matvec_launches", "syk_c128_arith"]
+            "syk_matvec_launches", "syk_c128_arith", "syk_status"]
 
 
 def _check(rc: int, what: str):
@@ -455,3 +456,8 @@ def syk_c128_arith(mode: int = -1) -> int:
     if rc < 0:
         _check(rc, "syk_c128_arith")
     return rc
+
+
+def syk_status(terms: Terms, reset: bool = False, stream=None) -> int:
+    """Status word of the term set's matvecs (synchronising): SYK_OK or SYK_ETIMEOUT."""
+    return int(load().syk_status(terms.ptr, int(bool(reset)), _stream(stream)))
