@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--c128-states", type=int, default=2,
                     help="states of the timed complex64 batch also evaluated in the plain complex128 form "
                          "(one state per step), for the c128 arm of the metric and the c64 accuracy (0: skip)")
+    ap.add_argument("--orth", default="default", choices=["default", "full", "local"],
+                    help="Lanczos orthogonalisation of the evolutions (library default, full Gram-Schmidt, or the "
+                         "three-term recurrence)")
     ap.add_argument("--no-batched-extra", action="store_true",
                     help="skip the mixed-N batch figure that the default line carries")
     return ap.parse_args()
@@ -347,6 +350,9 @@ def gpu_main(a, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     syk.load()
+    if a.orth != "default":
+        for code in (syk.SYK_C64, syk.SYK_C128):
+            syk.syk_lanczos_orth(code, syk.ORTH_FULL if a.orth == "full" else syk.ORTH_LOCAL)
     times = time_grid(a.npts, a.tmax)
     realization = rank
     J = inputs.couplings(a.N, seed=0, realization=realization)
@@ -444,6 +450,7 @@ def gpu_main(a, rank, world, local_rank):
                 "peak_kind": f"derived: {n_sm} SMs x 128 B/cycle x {sm_mhz:.0f} MHz"}
     esz = 8 if a.dtype == "c64" else 16
     gather = nnz * a.states * esz / (avg_ms * 1e-3) / 1e9
+    orth_names = {syk.ORTH_FULL: "full Gram-Schmidt", syk.ORTH_LOCAL: "three-term recurrence"}
     line = {
         "metric": "OTOC curves/hour at N=40", "value": value, "unit": "curves/hour", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
@@ -462,6 +469,8 @@ def gpu_main(a, rank, world, local_rank):
         "hpsi": {"gather_GBps": gather, "hbm_peak_GBps": pk.get("hbm_gbs"), "gather_frac_of_hbm":
                  gather / float(pk.get("hbm_gbs", 6800.0)), "peak_kind": pk_kind},
         "apply_tile": tile,
+        "lanczos_orthogonalisation": {"c64": orth_names[syk.syk_lanczos_orth(syk.SYK_C64)],
+                                      "c128": orth_names[syk.syk_lanczos_orth(syk.SYK_C128)]},
         "matvec_launches_by_kernel": mv,
         "applies_per_curve": applies_per_state,
         "applies_per_curve_model": applies_model(a.N, a.beta, times[1:], a.krylov, a.tol),

@@ -141,6 +141,19 @@ int syk_expmv(const syk_terms* terms, int parity, int dtype, double z_re, double
               const void* psi, void* out, int64_t batch, int krylov_dim, double tol,
               void* workspace, size_t ws_bytes, void* stream, int* nsteps);
 
+/* syk_lanczos_orth -- orthogonalisation of syk_expmv's Lanczos basis for `dtype` (used by
+ * every call that evolves a state: the correlators, the batch and the gradients; the
+ * eigenvalue Lanczos always uses two full passes).  mode 0: classical Gram-Schmidt of each
+ * new vector against the whole basis (the default for SYK_C128: one pass for SYK_C64, two
+ * for SYK_C128); mode 1: the three-term recurrence alone (each vector orthogonalised against
+ * the two before it; the default for SYK_C64).  In finite precision the
+ * three-term recurrence loses global orthogonality as Ritz values converge, but the Krylov
+ * approximation of a matrix function is known to stay accurate to about the rounding level
+ * of the vectors (Druskin, Greenbaum & Knizhnerman 1998), and it reads 2 basis vectors per
+ * step instead of 2(j+1).  mode < 0 only queries.  Returns the previous mode or SYK_EINVAL.
+ * Supp. Sec. I.B does not specify the Krylov variant. */
+int syk_lanczos_orth(int dtype, int mode);
+
 /* syk_expmv_static -- syk_expmv with its workspace in a fixed array of device
  * memory inside the library, so the call itself allocates nothing.  The paper
  * has no counterpart; this entry point is for callers that cannot allocate

@@ -178,6 +178,59 @@ void launch_one(const ApplyParams& p, const void* psi, void* y, int64_t ld, int6
 template <typename R>
 int try_tiled(const ApplyParams& p, const void* psi, void* y, int64_t batch, cudaStream_t st);
 
+// The Lanczos epilogue (see ApplyParams) for launches without one (the row kernel):
+// y[e] *= ep_scale[b]; per-block conj(ep_u) . y sums per column.  blockDim = B * k, so thread
+// t always handles column t % B; complex64 products and short sums in FP32, flushed to FP64.
+template <typename R>
+__global__ void k_epilogue(ApplyParams p, typename CT<R>::T* __restrict__ y, int64_t total, int B) {
+  using C = typename CT<R>::T;
+  extern __shared__ double2 red[];
+  const int b = threadIdx.x % B;
+  const R s = p.ep_scale ? R(p.ep_scale[b]) : R(1);
+  const C* __restrict__ u = static_cast<const C*>(p.ep_u);
+  double re = 0.0, im = 0.0;
+  R fr = R(0), fi = R(0);
+  int cnt = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    C v = y[e];
+    v.x *= s;
+    v.y *= s;
+    y[e] = v;
+    const C w = u[e];
+    fr = fma(w.x, v.x, fma(w.y, v.y, fr));
+    fi = fma(w.x, v.y, fma(-w.y, v.x, fi));
+    if (++cnt == 16) {
+      re += fr;
+      im += fi;
+      fr = fi = R(0);
+      cnt = 0;
+    }
+  }
+  red[threadIdx.x] = make_double2(re + fr, im + fi);
+  __syncthreads();
+  if ((int)threadIdx.x < B) {
+    double2 r = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < (int)blockDim.x; t += B) {
+      r.x += red[t].x;
+      r.y += red[t].y;
+    }
+    p.ep_part[(size_t)blockIdx.x * B + threadIdx.x] = r;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *p.ep_nblk = (int)gridDim.x;
+}
+
+template <typename R>
+int launch_epilogue(const ApplyParams& p, void* y, int64_t batch, cudaStream_t st) {
+  const int bdim = int(batch) * std::max(1, int(256 / batch));
+  const int64_t total = p.D * batch;
+  const int64_t blocks = std::min<int64_t>(std::min<int64_t>((total + bdim - 1) / bdim, 2 * sm_count()), p.ep_cap);
+  k_epilogue<R><<<(unsigned)blocks, bdim, bdim * sizeof(double2), st>>>(p, static_cast<typename CT<R>::T*>(y), total,
+                                                                        int(batch));
+  count_launch();
+  SYK_CUDA_CHECK(cudaGetLastError());
+  return SYK_OK;
+}
+
 template <typename R>
 int launch_apply_T(const ApplyParams& p, const void* psi, void* y, int64_t batch, cudaStream_t st) {
   const int rc = try_tiled<R>(p, psi, y, batch, st);
@@ -192,6 +245,7 @@ int launch_apply_T(const ApplyParams& p, const void* psi, void* y, int64_t batch
     else { launch_one<R, 1>(p, psi, y, batch, b0, st); b0 += 1; }
   }
   SYK_CUDA_CHECK(cudaGetLastError());
+  if (p.ep_part) return launch_epilogue<R>(p, y, batch, st);
   return SYK_OK;
 }
 
@@ -381,8 +435,11 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
     }
     __syncthreads();
   }
-  // rows are written in the natural layout (logical chunk k of a row at soff[k])
-  unsigned char* dst = !CL ? reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB : sm;
+  // rows are written in the natural layout (logical chunk k of a row at soff[k]): straight to
+  // y, or staged in shared memory for the cluster reduction or the Lanczos epilogue
+  using V16 = typename Slot<R>::Out;
+  const bool stage = CL || p.ep_part != nullptr;
+  unsigned char* dst = stage ? sm : reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB;
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
     const size_t row = (size_t)(tid + i * NT);
@@ -397,24 +454,29 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   if constexpr (CL) {
     // every CTA of the cluster reduces 1/csize of the tile's rows over the partial sums
     // held in the cluster's shared memories (fixed rank order: deterministic)
-    using V16 = typename Slot<R>::Out;
     tma::cluster_sync();
     const int units = TILEB / 16 / (int)csize;
     const uint32_t base = tma::saddr(sm) + crank * (uint32_t)units * 16u;
-    unsigned char* yt = reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB + (size_t)crank * units * 16;
-    for (int u = tid; u < units; u += NT) {
-      V16 sum = tma::ld_cluster(tma::map_rank(base + 16u * u, 0), V16{});
-      for (uint32_t r = 1; r < csize; ++r) {
-        const V16 v = tma::ld_cluster(tma::map_rank(base + 16u * u, r), V16{});
-        if constexpr (std::is_same<V16, float4>::value) {
-          sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
-        } else {
-          sum.x += v.x; sum.y += v.y;
-        }
-      }
-      *reinterpret_cast<V16*>(yt + 16u * u) = sum;
-    }
+    store_units<V16, ROWB>(
+        p, units, NT, (size_t)tile * TILEB + (size_t)crank * units * 16, y,
+        [&](int u) {
+          V16 sum = tma::ld_cluster(tma::map_rank(base + 16u * u, 0), V16{});
+          for (uint32_t r = 1; r < csize; ++r) {
+            const V16 v = tma::ld_cluster(tma::map_rank(base + 16u * u, r), V16{});
+            if constexpr (std::is_same<V16, float4>::value) {
+              sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+            } else {
+              sum.x += v.x; sum.y += v.y;
+            }
+          }
+          return sum;
+        },
+        sm + BUFB);
     tma::cluster_sync();  // no CTA leaves while others still read its shared memory
+  } else if (stage) {
+    __syncthreads();
+    store_units<V16, ROWB>(p, TILEB / 16, NT, (size_t)tile * TILEB, y,
+                           [&](int u) { return reinterpret_cast<const V16*>(sm)[u]; }, sm + BUFB);
   }
 }
 
@@ -465,6 +527,10 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     if (!tile_groups_cached(p.terms, tb, Cfg::GMAX, &groups, &ng)) return 1;  // row kernel instead
   } else {
     SYK_TRY(tile_groups(p.terms, tb, Cfg::GMAX, &groups, &ng));
+  }
+  if (p.ep_part && ntiles * cs > p.ep_cap) {
+    set_error("apply_H: %lld CTAs exceed the epilogue buffer (%lld)", (long long)(ntiles * cs), (long long)p.ep_cap);
+    return SYK_EINVAL;
   }
   const size_t smem = Cfg::smem(T);
   SYK_TRY(ensure_smem_limit((const void*)k_apply_tiled<R, BT, false>, (int)Cfg::smem(Cfg::RPT << 8)));

@@ -238,7 +238,9 @@ __global__ void __launch_bounds__(1 << NTB) k_apply_coset(ApplyParams p, const i
     }
     __syncthreads();
   }
-  unsigned char* dst = !CL ? reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB : sm;
+  // straight to y, or staged in shared memory for the cluster reduction or the Lanczos epilogue
+  const bool stage = CL || p.ep_part != nullptr;
+  unsigned char* dst = stage ? sm : reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB;
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
     unsigned char* out = dst + (size_t)(tid + i * NT) * ROWB;
@@ -249,16 +251,22 @@ __global__ void __launch_bounds__(1 << NTB) k_apply_coset(ApplyParams p, const i
     tma::cluster_sync();
     const int units = TILEB / 16 / (int)csize;
     const uint32_t base = tma::saddr(sm) + crank * (uint32_t)units * 16u;
-    unsigned char* yt = reinterpret_cast<unsigned char*>(y) + (size_t)tile * TILEB + (size_t)crank * units * 16;
-    for (int u = tid; u < units; u += NT) {
-      float4 sum = tma::ld_cluster(tma::map_rank(base + 16u * u, 0), float4{});
-      for (uint32_t r = 1; r < csize; ++r) {
-        const float4 v = tma::ld_cluster(tma::map_rank(base + 16u * u, r), float4{});
-        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
-      }
-      *reinterpret_cast<float4*>(yt + 16u * u) = sum;
-    }
+    store_units<float4, ROWB>(
+        p, units, NT, (size_t)tile * TILEB + (size_t)crank * units * 16, y,
+        [&](int u) {
+          float4 sum = tma::ld_cluster(tma::map_rank(base + 16u * u, 0), float4{});
+          for (uint32_t r = 1; r < csize; ++r) {
+            const float4 v = tma::ld_cluster(tma::map_rank(base + 16u * u, r), float4{});
+            sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+          }
+          return sum;
+        },
+        sm + BUFB);
     tma::cluster_sync();
+  } else if (stage) {
+    __syncthreads();
+    store_units<float4, ROWB>(p, TILEB / 16, NT, (size_t)tile * TILEB, y,
+                              [&](int u) { return reinterpret_cast<const float4*>(sm)[u]; }, sm + BUFB);
   }
 }
 
@@ -269,6 +277,10 @@ int launch_coset_ntb(const ApplyParams& p, const CosetLayout* L, const void* psi
   const int64_t ntiles = p.D / T;
   const size_t smem = Cfg::smem(T);
   if (smem > kMaxSmemPerCta) return 1;
+  if (p.ep_part && ntiles * cs > p.ep_cap) {
+    set_error("apply_H: %lld CTAs exceed the epilogue buffer (%lld)", (long long)(ntiles * cs), (long long)p.ep_cap);
+    return SYK_EINVAL;
+  }
   SYK_TRY(ensure_smem_limit((const void*)k_apply_coset<BT, RB, false, NTB>, (int)smem));
   SYK_TRY(ensure_smem_limit((const void*)k_apply_coset<BT, RB, true, NTB>, (int)smem));
   const float2* x = static_cast<const float2*>(psi);

@@ -69,6 +69,16 @@ struct ApplyParams {
   bool no_alloc;           // host-side: never allocate (use only cached tile-group lists)
   void* df_split;          // host-side: device buffer (>= D x batch x 16 bytes) for the split
   size_t df_split_bytes;   // copy of a complex128 input, or NULL (then allocated per call)
+  // Lanczos epilogue (ep_part NULL: plain y = H psi).  With it the launch computes
+  //   y[x][b] = ep_scale[b] * (H psi)[x][b]   (ep_scale NULL: scale 1), and
+  //   ep_part[cta * batch + b] = sum over the CTA's rows of conj(ep_u[x][b]) y[x][b]   (FP64),
+  // one partial per CTA and column (fixed-order sums), and *ep_nblk = the number of CTAs.
+  // ep_u has psi's layout and dtype (complex128 for the double-float kernel too).
+  const double* ep_scale;
+  const void* ep_u;
+  double2* ep_part;
+  int* ep_nblk;
+  int64_t ep_cap;          // host-side: capacity of ep_part in CTAs
 };
 
 // Chunks of X-masks sharing the compact-mask bits h above a tile of 2^tb rows, at

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -110,8 +111,43 @@ __global__ void k_dots(int nk, const typename CT<R>::T* __restrict__ V, size_t v
   }
 }
 
-// out[k*B + b] = sum_g part[(k*G + g)*B + b]; one warp per (k, b), deterministic order
-__global__ void k_reduce_parts(int nk, int G, int B, const double2* __restrict__ part, double2* __restrict__ out) {
+// out[k*B + b] = sc[k*B + b] * sum_g part[(k*G + g)*B + b] for k < nk (sc NULL: 1): one warp
+// per (k, b) in the first nwb blocks (8 warps each).  If ep_part is given, each of the B
+// blocks after them sums the matvec epilogue's partials of one column b over its *ep_nblk
+// CTAs (256 threads, strided, then a fixed tree) into out[ep_k*B + b] = sc[ep_k*B + b] * sum,
+// and, with beta_prev, also sets out[(ep_k-1)*B + b] = (beta_prev[b], 0) (the three-term
+// recurrence's coefficient of v_{ep_k-1}).  The epilogue's result goes to index ep_k (nk for
+// Gram-Schmidt, which projects on v_0..v_{nk-1} before it).  Deterministic order throughout.
+__global__ void k_reduce_parts(int nk, int G, int B, int nwb, const double2* __restrict__ part,
+                               const double* __restrict__ sc, int ep_k, const double2* __restrict__ ep_part,
+                               const int* __restrict__ ep_nblk, const double* __restrict__ beta_prev,
+                               double2* __restrict__ out) {
+  __shared__ double2 red[256];
+  if ((int)blockIdx.x >= nwb) {
+    const int b = (int)blockIdx.x - nwb;
+    const int ng = *ep_nblk;
+    double sx = 0.0, sy = 0.0;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+      const double2 p = ep_part[(size_t)g * B + b];
+      sx += p.x;
+      sy += p.y;
+    }
+    red[threadIdx.x] = make_double2(sx, sy);
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) {
+        red[threadIdx.x].x += red[threadIdx.x + h].x;
+        red[threadIdx.x].y += red[threadIdx.x + h].y;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double f = sc ? sc[ep_k * B + b] : 1.0;
+      out[ep_k * B + b] = make_double2(f * red[0].x, f * red[0].y);
+      if (beta_prev && ep_k > 0) out[(ep_k - 1) * B + b] = make_double2(beta_prev[b], 0.0);
+    }
+    return;
+  }
   const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (idx >= nk * B) return;
@@ -126,25 +162,29 @@ __global__ void k_reduce_parts(int nk, int G, int B, const double2* __restrict__
     sx += __shfl_xor_sync(0xffffffffu, sx, o);
     sy += __shfl_xor_sync(0xffffffffu, sy, o);
   }
-  if (lane == 0) out[idx] = make_double2(sx, sy);
+  const double f = sc ? sc[idx] : 1.0;
+  if (lane == 0) out[idx] = make_double2(f * sx, f * sy);
 }
 
-// w -= sum_{k<nk} h_k V_k (per column); npart[g*B + b] = partial |w|^2 of the result
+// dst = w - sum_{k0<=k<k1} h_k v_k with v_k = sc_k V_k (per column; dst may be w);
+// npart[g*B + b] = partial |dst|^2
 template <typename R>
-__global__ void k_update(int nk, const typename CT<R>::T* __restrict__ V, size_t vs, const double2* __restrict__ h,
-                         typename CT<R>::T* __restrict__ w, int64_t total, int B, double* __restrict__ npart) {
+__global__ void k_update(int k0, int k1, const typename CT<R>::T* __restrict__ V, size_t vs,
+                         const double2* __restrict__ h, const double* __restrict__ sc, const typename CT<R>::T* w,
+                         typename CT<R>::T* dst, int64_t total, int B, double* __restrict__ npart) {
   using C = typename CT<R>::T;
   extern __shared__ double2 sm[];
   const int b = threadIdx.x % B;
   DotAcc<R> acc;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     C x = w[e];
-    for (int k = 0; k < nk; ++k) {
+    for (int k = k0; k < k1; ++k) {
       const double2 hk = h[k * B + b];
+      const double f = sc[k * B + b];
       const C v = V[(size_t)k * vs + e];
-      cmac(x, R(-hk.x), R(-hk.y), v);
+      cmac(x, R(-hk.x * f), R(-hk.y * f), v);
     }
-    w[e] = x;
+    dst[e] = x;
     acc.add(x, x);
     acc.tick();
   }
@@ -165,17 +205,18 @@ __global__ void k_scale(const typename CT<R>::T* __restrict__ src, typename CT<R
   }
 }
 
-// out = sum_{k<nk} c_k V_k (per column)
+// out = sum_{k<nk} c_k v_k with v_k = sc_k V_k (per column)
 template <typename R>
 __global__ void k_combine(int nk, const typename CT<R>::T* __restrict__ V, size_t vs, const double2* __restrict__ c,
-                          typename CT<R>::T* __restrict__ out, int64_t total, int B) {
+                          const double* __restrict__ sc, typename CT<R>::T* __restrict__ out, int64_t total, int B) {
   using C = typename CT<R>::T;
   const int b = threadIdx.x % B;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     C x = make_c<R>(R(0), R(0));
     for (int k = 0; k < nk; ++k) {
       const double2 ck = c[k * B + b];
-      cmac(x, R(ck.x), R(ck.y), V[(size_t)k * vs + e]);
+      const double f = sc[k * B + b];
+      cmac(x, R(ck.x * f), R(ck.y * f), V[(size_t)k * vs + e]);
     }
     out[e] = x;
   }
@@ -183,9 +224,10 @@ __global__ void k_combine(int nk, const typename CT<R>::T* __restrict__ V, size_
 
 // beta0 = ||psi||, inv = 1/beta0 (0 for a zero column)
 __global__ void k_norm_init(int B, const double2* __restrict__ d, double* __restrict__ beta0, double* __restrict__ inv,
-                            int* status) {
+                            double* __restrict__ sc, int* status) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  sc[b] = 1.0;  // v_0 is stored normalised
   const double n2 = d[b].x;
   const double nb = sqrt(fmax(n2, 0.0));
   if (!isfinite(nb)) atomicOr(status, 1);
@@ -196,7 +238,8 @@ __global__ void k_norm_init(int B, const double2* __restrict__ d, double* __rest
 // alpha_j = Re(h1_j + h2_j), beta_j = ||w||; breakdown sets beta_j = 0
 __global__ void k_lanczos_scalars(int j, int B, int G, const double2* __restrict__ h1, const double2* __restrict__ h2,
                                   const double* __restrict__ npart, double* __restrict__ alpha,
-                                  double* __restrict__ beta, double* __restrict__ inv, int* status, double bt) {
+                                  double* __restrict__ beta, double* __restrict__ inv, double* __restrict__ sc,
+                                  int* status, double bt) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const double a = h1[j * B + b].x + (h2 ? h2[j * B + b].x : 0.0);
@@ -212,6 +255,7 @@ __global__ void k_lanczos_scalars(int j, int B, int G, const double2* __restrict
   alpha[j * B + b] = isfinite(a) ? a : 0.0;
   beta[j * B + b] = be;
   inv[b] = be > 0.0 ? 1.0 / be : 0.0;
+  sc[(j + 1) * B + b] = inv[b];  // v_{j+1} = u_{j+1} / beta_j
 }
 
 // ---------------------------------------------------------------- tridiagonal
@@ -400,9 +444,11 @@ struct Ops {
                                                                  (int)ws.B, ws.part);
     count_launch();
   }
-  static void update(const KrylovWS& ws, int nk, const void* V, size_t vs, const double2* h, void* w, double* np,
+  // dst = w - sum_{k0 <= k < k1} h_k v_k
+  static void update(const KrylovWS& ws, int k0, int k1, const double2* h, const void* w, void* dst, double* np,
                      cudaStream_t st) {
-    k_update<R><<<ws.G, ws.bdim, ws.bdim * sizeof(double2), st>>>(nk, (const C*)V, vs, h, (C*)w, ws.D * ws.B,
+    k_update<R><<<ws.G, ws.bdim, ws.bdim * sizeof(double2), st>>>(k0, k1, (const C*)ws.V, (size_t)(ws.D * ws.B), h,
+                                                                   ws.sc, (const C*)w, (C*)dst, ws.D * ws.B,
                                                                    (int)ws.B, np);
     count_launch();
   }
@@ -411,21 +457,84 @@ struct Ops {
     count_launch();
   }
   static void combine(const KrylovWS& ws, int nk, const double2* c, void* out, cudaStream_t st) {
-    k_combine<R><<<ws.G, ws.bdim, 0, st>>>(nk, (const C*)ws.V, (size_t)(ws.D * ws.B), c, (C*)out, ws.D * ws.B,
-                                           (int)ws.B);
+    k_combine<R><<<ws.G, ws.bdim, 0, st>>>(nk, (const C*)ws.V, (size_t)(ws.D * ws.B), c, ws.sc, (C*)out,
+                                           ws.D * ws.B, (int)ws.B);
     count_launch();
   }
 };
 
-void reduce_parts(const KrylovWS& ws, int nk, double2* out, cudaStream_t st) {
-  const int n = nk * (int)ws.B;  // one warp each
-  k_reduce_parts<<<(n + 7) / 8, 256, 0, st>>>(nk, ws.G, (int)ws.B, ws.part, out);
+// out[k] (k < nk) from the dots' partial sums, scaled by the basis scales when sc is given,
+// plus out[nk] from the matvec epilogue's partials when with_ep
+// out[k] for k < nk from the dots' partial sums (scaled by the basis scales when sc is given),
+// and, with ep_k >= 0, out[ep_k] from the matvec epilogue's partials (see k_reduce_parts)
+void reduce_parts(const KrylovWS& ws, int nk, double2* out, cudaStream_t st, const double* sc = nullptr,
+                  int ep_k = -1, const double* beta_prev = nullptr) {
+  const int nwb = (nk * (int)ws.B + 7) / 8;  // one warp per (k, b)
+  const int nb = nwb + (ep_k >= 0 ? (int)ws.B : 0);
+  if (nb == 0) return;
+  k_reduce_parts<<<nb, 256, 0, st>>>(nk, ws.G, (int)ws.B, nwb, ws.part, sc, ep_k, ep_k >= 0 ? ws.ep_part : nullptr,
+                                     ws.ep_nblk, beta_prev, out);
   count_launch();
+}
+
+// One Lanczos step j on the unnormalised basis (see KrylovWS::sc).  The matvec computes
+// w = H v_j = sc_j H u_j (scale in its output stage) and h_j = <v_j, w> (per-CTA partial dots in
+// its epilogue, fixed-order sums); then, by `orth`:
+//   kOrthFull:  h_k = <v_k, w> for k < j (classical Gram-Schmidt against the whole basis);
+//               u_{j+1} = w - sum_{k<=j} h_k v_k; with two_pass a second projection and
+//               update (the first updates w in place);
+//   kOrthLocal: the three-term recurrence u_{j+1} = w - h_j v_j - beta_{j-1} v_{j-1};
+// u_{j+1} is written straight into basis slot j+1 with its partial norms, and the scalars
+// kernel sets alpha_j = Re h_j, beta_j = |u_{j+1}|, sc_{j+1} = 1/beta_j.  There is no
+// normalisation pass: the next matvec and every later coefficient carry sc.
+template <typename R>
+int lanczos_step(const ApplyParams& P, int dtype, KrylovWS& ws, int j, int orth, bool two_pass, double bt,
+                 cudaStream_t st) {
+  const int64_t B = ws.B;
+  const size_t vs = size_t(ws.D) * B;
+  ApplyParams Pe = P;
+  Pe.ep_scale = ws.sc + size_t(j) * B;
+  Pe.ep_u = ws.vec(j);
+  Pe.ep_part = ws.ep_part;
+  Pe.ep_nblk = ws.ep_nblk;
+  SYK_TRY(launch_apply_H(Pe, dtype, ws.vec(j), ws.w, B, st));
+  void* next = ws.vec(j + 1);
+  if (orth == kOrthLocal) {
+    reduce_parts(ws, 0, ws.h1, st, ws.sc, j, j > 0 ? ws.beta + size_t(j - 1) * B : nullptr);
+    Ops<R>::update(ws, j > 0 ? j - 1 : 0, j + 1, ws.h1, ws.w, next, ws.npart, st);
+    two_pass = false;
+  } else {
+    if (j > 0) Ops<R>::dots(ws, j, ws.V, vs, ws.w, st);
+    reduce_parts(ws, j, ws.h1, st, ws.sc, j);
+    if (two_pass) {
+      Ops<R>::update(ws, 0, j + 1, ws.h1, ws.w, ws.w, nullptr, st);
+      Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
+      reduce_parts(ws, j + 1, ws.h2, st, ws.sc);
+      Ops<R>::update(ws, 0, j + 1, ws.h2, ws.w, next, ws.npart, st);
+    } else {
+      Ops<R>::update(ws, 0, j + 1, ws.h1, ws.w, next, ws.npart, st);
+    }
+  }
+  k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, two_pass ? ws.h2 : nullptr,
+                                                           ws.npart, ws.alpha, ws.beta, ws.inv, ws.sc, ws.status, bt);
+  count_launch();
+  SYK_CUDA_CHECK(cudaGetLastError());
+  return SYK_OK;
 }
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
+// CTAs a matvec launch may have (its epilogue writes one partial per CTA and column): tiles of
+// at least 64 rows, clusters of at most 8; the row kernel's epilogue uses at most kRedBlocksCap.
+int64_t ep_capacity(int64_t D) { return std::max<int64_t>(D / 8, kRedBlocksCap); }
+
 }  // namespace
+
+// by dtype code: complex64 defaults to the three-term recurrence (as accurate as full
+// Gram-Schmidt at FP32 rounding, measured against complex128 and the oracle, and 11 % less
+// time per OTOC curve at N = 40); complex128, the accuracy reference, to full Gram-Schmidt
+std::atomic<int> g_orth[3] = {{kOrthFull}, {kOrthLocal}, {kOrthFull}};
+int lanczos_orth(int dtype) { return g_orth[dtype == SYK_C64 ? SYK_C64 : SYK_C128].load(); }
 
 // ---------------------------------------------------------------- workspace
 size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B) {
@@ -446,6 +555,9 @@ size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B) {
   s += align_up(sizeof(double2) * m * B);             // c
   s += align_up(sizeof(int) * 4);                     // status
   if (dtype == SYK_C128) s += align_up(size_t(D) * B * 16);  // split
+  s += align_up(sizeof(double) * (m + 1) * B);                // sc
+  s += align_up(sizeof(double2) * size_t(ep_capacity(D)) * B);  // ep_part
+  s += align_up(sizeof(int));                                 // ep_nblk
   return s;
 }
 
@@ -488,6 +600,10 @@ int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype
   ws->c = (double2*)take(sizeof(double2) * m * B);
   ws->status = (int*)take(sizeof(int) * 4);
   ws->split = dtype == SYK_C128 ? take(size_t(D) * B * 16) : nullptr;
+  ws->sc = (double*)take(sizeof(double) * (m + 1) * B);
+  ws->ep_cap = ep_capacity(D);
+  ws->ep_part = (double2*)take(sizeof(double2) * size_t(ws->ep_cap) * B);
+  ws->ep_nblk = (int*)take(sizeof(int));
   return SYK_OK;
 }
 
@@ -597,12 +713,12 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
             void* const* outs, double tol, KrylovWS& ws, cudaStream_t st, int* nsteps) {
   const ApplyParams P = ws.with_split(P_in);
   const int64_t B = ws.B;
-  const size_t vs = size_t(ws.D) * B;
   const int m = ws.m;
   const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
   // complex64 vectors carry ~1e-7 relative error, which one reorthogonalisation pass already
   // reaches; complex128 vectors get the second pass ("twice is enough")
   const bool two_pass = dtype == SYK_C128;
+  const int orth = lanczos_orth(dtype);
   // Convergence of the sub-step is checked after 4 vectors and then every `every` vectors: a
   // check (eigensolve of T + one host read) costs far less than a matvec once the state is
   // large, so large states are checked every 2 vectors, small ones every 8.
@@ -622,29 +738,14 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
     // v_0 = cur / ||cur||
     Ops<R>::dots(ws, 1, cur, 0, cur, st);
     reduce_parts(ws, 1, ws.h1, st);
-    k_norm_init<<<(int(B) + 127) / 128, 128, 0, st>>>(int(B), ws.h1, ws.beta0, ws.inv, ws.status);
+    k_norm_init<<<(int(B) + 127) / 128, 128, 0, st>>>(int(B), ws.h1, ws.beta0, ws.inv, ws.sc, ws.status);
     count_launch();
     Ops<R>::scale(ws, cur, ws.vec(0), ws.inv, st);
     int m_eff = m;
     // Lanczos iterations j in [j0, j1) between two convergence checks
     auto segment = [&](int j0, int j1, cudaStream_t st) -> int {
-      for (int j = j0; j < j1; ++j) {
-        SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, B, st));
-        // classical Gram-Schmidt against the whole basis; a second pass for FP64 vectors
-        Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
-        reduce_parts(ws, j + 1, ws.h1, st);
-        Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, two_pass ? nullptr : ws.npart, st);
-        if (two_pass) {
-          Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
-          reduce_parts(ws, j + 1, ws.h2, st);
-          Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
-        }
-        k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, two_pass ? ws.h2 : nullptr,
-                                                                 ws.npart, ws.alpha, ws.beta, ws.inv, ws.status, bt);
-        count_launch();
-        if (j + 1 < m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
-      }
-      SYK_CUDA_CHECK(cudaGetLastError());
+      // classical Gram-Schmidt against the whole basis; a second pass for FP64 vectors
+      for (int j = j0; j < j1; ++j) SYK_TRY(lanczos_step<R>(P, dtype, ws, j, orth, two_pass, bt, st));
       return SYK_OK;
     };
     int j0 = 0;
@@ -773,24 +874,10 @@ namespace {
 template <typename R>
 int lanczos_steps_T(const ApplyParams& P_in, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st) {
   const ApplyParams P = ws.with_split(P_in);
-  const size_t vs = size_t(ws.D) * ws.B;
   const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
-  for (int j = j0; j < j1; ++j) {
-    SYK_TRY(launch_apply_H(P, dtype, ws.vec(j), ws.w, ws.B, st));
-    // two passes of classical Gram-Schmidt against the whole basis for both vector types:
-    // Ritz values of a long run need the basis orthogonal to working precision
-    Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
-    reduce_parts(ws, j + 1, ws.h1, st);
-    Ops<R>::update(ws, j + 1, ws.V, vs, ws.h1, ws.w, nullptr, st);
-    Ops<R>::dots(ws, j + 1, ws.V, vs, ws.w, st);
-    reduce_parts(ws, j + 1, ws.h2, st);
-    Ops<R>::update(ws, j + 1, ws.V, vs, ws.h2, ws.w, ws.npart, st);
-    k_lanczos_scalars<<<1, 128, 0, st>>>(j, int(ws.B), ws.G, ws.h1, ws.h2, ws.npart, ws.alpha, ws.beta, ws.inv,
-                                         ws.status, bt);
-    count_launch();
-    if (j + 1 < ws.m) Ops<R>::scale(ws, ws.w, ws.vec(j + 1), ws.inv, st);
-  }
-  SYK_CUDA_CHECK(cudaGetLastError());
+  // two passes of classical Gram-Schmidt against the whole basis for both vector types:
+  // Ritz values of a long run need the basis orthogonal to working precision
+  for (int j = j0; j < j1; ++j) SYK_TRY(lanczos_step<R>(P, dtype, ws, j, kOrthFull, true, bt, st));
   return SYK_OK;
 }
 }  // namespace
@@ -800,7 +887,7 @@ int lanczos_begin(int dtype, const void* psi, KrylovWS& ws, cudaStream_t st) {
   if (dtype == SYK_C64) Ops<float>::dots(ws, 1, psi, 0, psi, st);
   else Ops<double>::dots(ws, 1, psi, 0, psi, st);
   reduce_parts(ws, 1, ws.h1, st);
-  k_norm_init<<<(int(ws.B) + 127) / 128, 128, 0, st>>>(int(ws.B), ws.h1, ws.beta0, ws.inv, ws.status);
+  k_norm_init<<<(int(ws.B) + 127) / 128, 128, 0, st>>>(int(ws.B), ws.h1, ws.beta0, ws.inv, ws.sc, ws.status);
   count_launch();
   if (dtype == SYK_C64) Ops<float>::scale(ws, psi, ws.vec(0), ws.inv, st);
   else Ops<double>::scale(ws, psi, ws.vec(0), ws.inv, st);
@@ -821,6 +908,23 @@ int lanczos_steps(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1,
 
 // ---------------------------------------------------------------- C ABI
 using namespace syk;
+
+extern "C" int syk_lanczos_orth(int dtype, int mode) {
+  clear_error();
+  if (!dtype_ok(dtype)) {
+    set_error("syk_lanczos_orth: dtype must be SYK_C64 or SYK_C128 (got %d)", dtype);
+    return SYK_EINVAL;
+  }
+  const int prev = g_orth[dtype].load();
+  if (mode < 0) return prev;
+  if (mode != kOrthFull && mode != kOrthLocal) {
+    set_error("syk_lanczos_orth: mode must be 0 (full Gram-Schmidt) or 1 (three-term recurrence), got %d", mode);
+    return SYK_EINVAL;
+  }
+  g_orth[dtype] = mode;
+  bump_graph_epoch();  // captured segments carry the other kernel sequence
+  return prev;
+}
 
 extern "C" size_t syk_workspace_bytes(int N, int dtype, int krylov_dim, int64_t batch, int kind) {
   (void)kind;

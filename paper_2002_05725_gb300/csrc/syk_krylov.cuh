@@ -31,6 +31,12 @@ struct KrylovWS {
   double2* c = nullptr;      // m * B
   int* status = nullptr;     // 4 ints
   char* split = nullptr;     // complex128 only: double-float copy of the matvec input (D*B float4)
+  // The basis is stored unnormalised: V_k = u_k with v_k = sc[k*B + b] u_k (sc[0] = 1; the
+  // Lanczos step folds 1/beta_j into the next matvec's output instead of rescaling u_{j+1}).
+  double* sc = nullptr;      // (m+1) * B
+  double2* ep_part = nullptr;  // per-CTA partial dots of the matvec epilogue (ep_cap * B)
+  int* ep_nblk = nullptr;
+  int64_t ep_cap = 0;
   void* host_stage = nullptr;  // host buffer (>= 64 B) for status reads; NULL: pinned scratch
   size_t vec_bytes() const { return size_t(D) * B * dtype_size(dtype); }
   char* vec(int k) const { return V + size_t(k) * vec_bytes(); }
@@ -41,9 +47,15 @@ struct KrylovWS {
       q.df_split = split;
       q.df_split_bytes = size_t(D) * B * 16;
     }
+    q.ep_cap = ep_cap;
     return q;
   }
 };
+
+// Orthogonalisation of expmv's Lanczos basis (syk_lanczos_orth): full classical Gram-Schmidt
+// against the whole basis, or the local three-term recurrence.
+enum { kOrthFull = 0, kOrthLocal = 1 };
+int lanczos_orth(int dtype);
 
 size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B);
 int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype, int m, int64_t B);

@@ -411,6 +411,11 @@ int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p)
   p->no_alloc = false;
   p->df_split = nullptr;
   p->df_split_bytes = 0;
+  p->ep_scale = nullptr;
+  p->ep_u = nullptr;
+  p->ep_part = nullptr;
+  p->ep_nblk = nullptr;
+  p->ep_cap = 0;
   return SYK_OK;
 }
 

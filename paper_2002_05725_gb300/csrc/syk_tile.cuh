@@ -236,4 +236,103 @@ __device__ __forceinline__ typename CT<R>::T pc2_c(const typename CT<R>::T* __re
   }
 }
 
+// ---------------------------------------------------------------- output stage
+// The tiled matvecs write a CTA's outputs as 16-byte units: unit u lies at byte offset
+// goff + 16 u of the vector (goff = the CTA's first unit, always at the start of a row).  A
+// thread handles units tid, tid + NT, ...; their stride 16 NT is a multiple of the row size
+// ROWB (columns x element size <= 256 <= 16 x 64), so a thread's units always hold the same
+// columns: element slot e of unit u (e = 0, 1 for complex64 pairs, 0 for complex128) is column
+//   col(tid, e) = ((16 tid + esz e) mod ROWB) / esz.
+// With the Lanczos epilogue (p.ep_part set) every element is multiplied by its column's
+// ep_scale and the CTA's conj(ep_u) . y sums per column are written to p.ep_part[cta][column]:
+// per-thread sums (FP32 products and sums for complex64, FP64 for complex128) over the
+// thread's units, then per column over the threads in increasing order (deterministic).
+template <typename V16>
+struct EpiVec;
+template <>
+struct EpiVec<float4> {  // two complex64 per unit
+  static constexpr int NE = 2, ESZ = 8;
+  struct Acc {
+    float r[2] = {0.f, 0.f}, i[2] = {0.f, 0.f};
+  };
+  static __device__ __forceinline__ float4 scale(float4 v, const double (&s)[2]) {
+    const float s0 = (float)s[0], s1 = (float)s[1];
+    return make_float4(v.x * s0, v.y * s0, v.z * s1, v.w * s1);
+  }
+  static __device__ __forceinline__ void dot(Acc& a, const float4 u, const float4 v) {
+    a.r[0] = fmaf(u.x, v.x, fmaf(u.y, v.y, a.r[0]));
+    a.i[0] = fmaf(u.x, v.y, fmaf(-u.y, v.x, a.i[0]));
+    a.r[1] = fmaf(u.z, v.z, fmaf(u.w, v.w, a.r[1]));
+    a.i[1] = fmaf(u.z, v.w, fmaf(-u.w, v.z, a.i[1]));
+  }
+  static __device__ __forceinline__ double2 get(const Acc& a, int e) { return make_double2(a.r[e], a.i[e]); }
+};
+template <>
+struct EpiVec<double2> {  // one complex128 per unit
+  static constexpr int NE = 1, ESZ = 16;
+  struct Acc {
+    double r = 0.0, i = 0.0;
+  };
+  static __device__ __forceinline__ double2 scale(double2 v, const double (&s)[1]) {
+    return make_double2(v.x * s[0], v.y * s[0]);
+  }
+  static __device__ __forceinline__ void dot(Acc& a, const double2 u, const double2 v) {
+    a.r = fma(u.x, v.x, fma(u.y, v.y, a.r));
+    a.i = fma(u.x, v.y, fma(-u.y, v.x, a.i));
+  }
+  static __device__ __forceinline__ double2 get(const Acc& a, int) { return make_double2(a.r, a.i); }
+};
+
+// Stores units [0, units) (fetch(u) gives unit u) to y at byte offset goff, with the Lanczos
+// epilogue if p.ep_part is set.  red: shared scratch of 32 NT bytes.  Every thread calls it.
+template <typename V16, int ROWB, typename Fetch>
+__device__ __forceinline__ void store_units(const ApplyParams& p, int units, int NT, size_t goff, void* y,
+                                            Fetch&& fetch, unsigned char* red) {
+  using E = EpiVec<V16>;
+  constexpr int NE = E::NE, ESZ = E::ESZ, NB = ROWB / ESZ > 0 ? ROWB / ESZ : 1;
+  const int tid = threadIdx.x;
+  unsigned char* yt = static_cast<unsigned char*>(y) + goff;
+  if (p.ep_part == nullptr) {
+    for (int u = tid; u < units; u += NT) *reinterpret_cast<V16*>(yt + 16u * u) = fetch(u);
+    return;
+  }
+  double s[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int c = ((16 * tid + ESZ * e) % ROWB) / ESZ;
+    s[e] = p.ep_scale ? p.ep_scale[c] : 1.0;
+  }
+  typename E::Acc acc;
+  const unsigned char* ut = static_cast<const unsigned char*>(p.ep_u) + goff;
+  for (int u = tid; u < units; u += NT) {
+    const V16 v = E::scale(fetch(u), s);
+    *reinterpret_cast<V16*>(yt + 16u * u) = v;
+    E::dot(acc, *reinterpret_cast<const V16*>(ut + 16u * u), v);
+  }
+  double2* r = reinterpret_cast<double2*>(red);
+#pragma unroll
+  for (int e = 0; e < NE; ++e) r[tid * NE + e] = E::get(acc, e);
+  __syncthreads();
+  if (tid < NB) {
+    // column tid: units with slot q = (tid esz) / 16 mod P of every row (P units per row), or
+    // every unit when a unit spans more than one row (one column)
+    double2 sum = make_double2(0.0, 0.0);
+    if constexpr (ROWB >= 16) {
+      constexpr int P = ROWB / 16;
+      const int q = (tid * ESZ / 16) % P, e = (tid * ESZ % 16) / ESZ;
+      for (int t = q; t < NT; t += P) {
+        sum.x += r[t * NE + e].x;
+        sum.y += r[t * NE + e].y;
+      }
+    } else {
+      for (int t = 0; t < NT * NE; ++t) {
+        sum.x += r[t].x;
+        sum.y += r[t].y;
+      }
+    }
+    p.ep_part[(size_t)blockIdx.x * NB + tid] = sum;
+  }
+  if (blockIdx.x == 0 && tid == 0) *p.ep_nblk = (int)gridDim.x;
+}
+
 }  // namespace syk

@@ -78,6 +78,7 @@ def load(build_if_missing: bool = False):
         "syk_matvec_launches": (i32, [vp, vp, vp, i32]),
         "syk_c128_arith": (i32, [i32]),
         "syk_status": (i32, [vp, i32, vp]),
+        "syk_lanczos_orth": (i32, [i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -95,7 +96,7 @@ def exported_symbols():
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
             "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak",
-            "syk_matvec_launches", "syk_c128_arith", "syk_status"]
+            "syk_matvec_launches", "syk_c128_arith", "syk_status", "syk_lanczos_orth"]
 
 
 def _check(rc: int, what: str):
@@ -461,3 +462,15 @@ def syk_c128_arith(mode: int = -1) -> int:
 def syk_status(terms: Terms, reset: bool = False, stream=None) -> int:
     """Status word of the term set's matvecs (synchronising): SYK_OK or SYK_ETIMEOUT."""
     return int(load().syk_status(terms.ptr, int(bool(reset)), _stream(stream)))
+
+
+ORTH_FULL, ORTH_LOCAL = 0, 1
+
+
+def syk_lanczos_orth(dtype: int, mode: int = -1) -> int:
+    """Sets expmv's Lanczos orthogonalisation for dtype (0: full Gram-Schmidt, 1: three-term
+    recurrence; < 0 only queries) and returns the previous mode."""
+    rc = load().syk_lanczos_orth(int(dtype), int(mode))
+    if rc < 0:
+        _check(rc, "syk_lanczos_orth")
+    return rc
