@@ -76,17 +76,18 @@ extern "C" int syk_correlator_G(const syk_terms* terms, double beta, int i, cons
   SYK_TRY(device_input(psi0, vb, sc, &psi));
   KrylovWS ws;
   SYK_TRY(krylov_ws_carve(&ws, wsp, wsb, terms->D, dtype, krylov_dim, B));
+  SYK_TRY(chain_begin(ws, st));
   double2* r = static_cast<double2*>(res);
   // phi = e^{-beta H/2} psi~ (even sector), Z = <phi|phi>
-  SYK_TRY(expmv_impl(P0, dtype, {-0.5 * beta, 0.0}, psi, a, B, tol, ws, st, nullptr));
+  SYK_TRY(expmv_chain(P0, dtype, {-0.5 * beta, 0.0}, psi, a, B, tol, ws, st));
   SYK_TRY(dot_columns(a, a, terms->D, B, dtype, ws, r + size_t(nt) * B, st));
   SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, a, b, B, st));  // b = chi_i phi (odd)
   double tcur = 0.0;
   for (int k = 0; k < nt; ++k) {
     const double dt = t[k] - tcur;
     if (dt > 0.0) {
-      SYK_TRY(expmv_impl(P0, dtype, {0.0, -dt}, a, a, B, tol, ws, st, nullptr));
-      SYK_TRY(expmv_impl(P1, dtype, {0.0, -dt}, b, b, B, tol, ws, st, nullptr));
+      SYK_TRY(expmv_chain(P0, dtype, {0.0, -dt}, a, a, B, tol, ws, st));
+      SYK_TRY(expmv_chain(P1, dtype, {0.0, -dt}, b, b, B, tol, ws, st));
       tcur = t[k];
     }
     SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, b, tmp, B, st));  // chi_i U chi_i phi (even)
@@ -94,7 +95,7 @@ extern "C" int syk_correlator_G(const syk_terms* terms, double beta, int i, cons
   }
   std::vector<double2> h(size_t(nt + 1) * B);
   SYK_CUDA_CHECK(cudaMemcpyAsync(h.data(), r, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
-  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  SYK_TRY(chain_end(ws, st));  // synchronises st; device-side errors of the evolutions
   prof_collect();
   for (int64_t s = 0; s < B; ++s) {
     const double z = h[size_t(nt) * B + s].x;
@@ -135,31 +136,32 @@ int otoc_impl(const syk_terms* terms, double beta, const double* x, int i, int j
   SYK_TRY(device_input(psi0, vb, sc, &psi));
   KrylovWS ws;
   SYK_TRY(krylov_ws_carve(&ws, wsp, wsb, terms->D, dtype, krylov_dim, B));
+  SYK_TRY(chain_begin(ws, st));
   double2* r = static_cast<double2*>(res);
   // ua = phi = rho^{x4/2} psi~ (even); ub = a0 = rho^{x3} chi_j phi (odd)
-  SYK_TRY(expmv_impl(P0, dtype, {-beta * x[3] / 2.0, 0.0}, psi, ua, B, tol, ws, st, nullptr));
+  SYK_TRY(expmv_chain(P0, dtype, {-beta * x[3] / 2.0, 0.0}, psi, ua, B, tol, ws, st));
   SYK_TRY(launch_apply_chi(terms->N, j, 0, dtype, ua, tmp, B, st));
-  SYK_TRY(expmv_impl(P1, dtype, {-beta * x[2], 0.0}, tmp, ub, B, tol, ws, st, nullptr));
+  SYK_TRY(expmv_chain(P1, dtype, {-beta * x[2], 0.0}, tmp, ub, B, tol, ws, st));
   double tcur = 0.0;
   for (int k = 0; k < nt; ++k) {
     const double tk = t[k], dt = tk - tcur;
     if (dt > 0.0) {
-      SYK_TRY(expmv_impl(P0, dtype, {0.0, -dt}, ua, ua, B, tol, ws, st, nullptr));  // U(t) phi
-      SYK_TRY(expmv_impl(P1, dtype, {0.0, -dt}, ub, ub, B, tol, ws, st, nullptr));  // U(t) a0
+      SYK_TRY(expmv_chain(P0, dtype, {0.0, -dt}, ua, ua, B, tol, ws, st));  // U(t) phi
+      SYK_TRY(expmv_chain(P1, dtype, {0.0, -dt}, ub, ub, B, tol, ws, st));  // U(t) a0
       tcur = tk;
     }
     SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, ua, pr, B, st));  // p (odd)
     SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, ub, qs, B, st));  // q (even)
     // r = rho^{x1} U^dag p and s = rho^{x2} U^dag q: the exponentials commute, so each is one
     // Krylov evolution with z = -beta x + i t
-    SYK_TRY(expmv_impl(P1, dtype, {-beta * x[0], tk}, pr, pr, B, tol, ws, st, nullptr));  // r (odd)
-    SYK_TRY(expmv_impl(P0, dtype, {-beta * x[1], tk}, qs, qs, B, tol, ws, st, nullptr));  // s (even)
+    SYK_TRY(expmv_chain(P1, dtype, {-beta * x[0], tk}, pr, pr, B, tol, ws, st));  // r (odd)
+    SYK_TRY(expmv_chain(P0, dtype, {-beta * x[1], tk}, qs, qs, B, tol, ws, st));  // s (even)
     SYK_TRY(launch_apply_chi(terms->N, j, 0, dtype, qs, tmp, B, st));     // chi_j s (odd)
     SYK_TRY(dot_columns(pr, tmp, terms->D, B, dtype, ws, r + size_t(k) * B, st));
   }
   std::vector<double2> h(size_t(nt) * B);
   SYK_CUDA_CHECK(cudaMemcpyAsync(h.data(), r, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
-  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  SYK_TRY(chain_end(ws, st));  // synchronises st; device-side errors of the evolutions
   prof_collect();
   for (size_t e = 0; e < h.size(); ++e) {
     F_re_im[2 * e] = h[e].x;
@@ -239,9 +241,10 @@ extern "C" int syk_correlator_G_imag(const syk_terms* terms, double beta, int i,
   SYK_TRY(device_input(psi0, vb, sc, &psi));
   KrylovWS ws;
   SYK_TRY(krylov_ws_carve(&ws, wsp, wsb, terms->D, dtype, krylov_dim, B));
+  SYK_TRY(chain_begin(ws, st));
   double2* r = static_cast<double2*>(res);
   // x = e^{-beta H/2} psi~ (even), Z = <x|x>; w(tau) = e^{tau H} x (even), y(tau) = e^{-tau H} chi_i x (odd)
-  SYK_TRY(expmv_impl(P0, dtype, {-0.5 * beta, 0.0}, psi, x, B, tol, ws, st, nullptr));
+  SYK_TRY(expmv_chain(P0, dtype, {-0.5 * beta, 0.0}, psi, x, B, tol, ws, st));
   SYK_TRY(dot_columns(x, x, terms->D, B, dtype, ws, r + size_t(ntau) * B, st));
   SYK_CUDA_CHECK(cudaMemcpyAsync(w, x, vb, cudaMemcpyDeviceToDevice, st));
   SYK_TRY(launch_apply_chi(terms->N, i, 0, dtype, x, y, B, st));
@@ -249,8 +252,8 @@ extern "C" int syk_correlator_G_imag(const syk_terms* terms, double beta, int i,
   for (int k = 0; k < ntau; ++k) {
     const double dt = tau[k] - tcur;
     if (dt > 0.0) {
-      SYK_TRY(expmv_impl(P0, dtype, {dt, 0.0}, w, w, B, tol, ws, st, nullptr));
-      SYK_TRY(expmv_impl(P1, dtype, {-dt, 0.0}, y, y, B, tol, ws, st, nullptr));
+      SYK_TRY(expmv_chain(P0, dtype, {dt, 0.0}, w, w, B, tol, ws, st));
+      SYK_TRY(expmv_chain(P1, dtype, {-dt, 0.0}, y, y, B, tol, ws, st));
       tcur = tau[k];
     }
     SYK_TRY(launch_apply_chi(terms->N, i, 1, dtype, y, tmp, B, st));  // chi_i e^{-tau H} chi_i x (even)
@@ -258,7 +261,7 @@ extern "C" int syk_correlator_G_imag(const syk_terms* terms, double beta, int i,
   }
   std::vector<double2> h(size_t(ntau + 1) * B);
   SYK_CUDA_CHECK(cudaMemcpyAsync(h.data(), r, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
-  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  SYK_TRY(chain_end(ws, st));  // synchronises st; device-side errors of the evolutions
   prof_collect();
   for (int64_t s2 = 0; s2 < B; ++s2) {
     const double z = h[size_t(ntau) * B + s2].x;

@@ -176,17 +176,31 @@ __global__ void k_update(int k0, int k1, const typename CT<R>::T* __restrict__ V
   extern __shared__ double2 sm[];
   const int b = threadIdx.x % B;
   DotAcc<R> acc;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    C x = w[e];
+  // U elements per thread and pass (same column: the stride is a multiple of B), so that the
+  // loads of w and of every basis vector for all U are in flight together
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < total; e0 += U * stride) {
+    C x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * stride < total) x[u] = w[e0 + u * stride];
     for (int k = k0; k < k1; ++k) {
       const double2 hk = h[k * B + b];
       const double f = sc[k * B + b];
-      const C v = V[(size_t)k * vs + e];
-      cmac(x, R(-hk.x * f), R(-hk.y * f), v);
+      const R cr = R(-hk.x * f), ci = R(-hk.y * f);
+      const C* __restrict__ Vk = V + (size_t)k * vs;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (e0 + u * stride < total) cmac(x[u], cr, ci, Vk[e0 + u * stride]);
     }
-    dst[e] = x;
-    acc.add(x, x);
-    acc.tick();
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * stride < total) {
+        dst[e0 + u * stride] = x[u];
+        acc.add(x[u], x[u]);
+        acc.tick();
+      }
   }
   double2 r = block_reduce_cols(acc.get(), B, sm);
   if ((int)threadIdx.x < B && npart) npart[(size_t)blockIdx.x * B + threadIdx.x] = r.x;
@@ -235,16 +249,20 @@ __global__ void k_norm_init(int B, const double2* __restrict__ d, double* __rest
   inv[b] = nb > 0.0 ? 1.0 / nb : 0.0;
 }
 
-// alpha_j = Re(h1_j + h2_j), beta_j = ||w||; breakdown sets beta_j = 0
+// alpha_j = Re(h1_j + h2_j), beta_j = ||w||; breakdown sets beta_j = 0.  One warp per column:
+// the G partial norms are summed lane-strided, then by a fixed shuffle tree.
 __global__ void k_lanczos_scalars(int j, int B, int G, const double2* __restrict__ h1, const double2* __restrict__ h2,
                                   const double* __restrict__ npart, double* __restrict__ alpha,
                                   double* __restrict__ beta, double* __restrict__ inv, double* __restrict__ sc,
                                   int* status, double bt) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (b >= B) return;
-  const double a = h1[j * B + b].x + (h2 ? h2[j * B + b].x : 0.0);
   double n2 = 0.0;
-  for (int g = 0; g < G; ++g) n2 += npart[(size_t)g * B + b];
+  for (int g = lane; g < G; g += 32) n2 += npart[(size_t)g * B + b];
+  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  if (lane != 0) return;
+  const double a = h1[j * B + b].x + (h2 ? h2[j * B + b].x : 0.0);
   double be = sqrt(fmax(n2, 0.0));
   if (!isfinite(a) || !isfinite(be)) {
     atomicOr(status, 1);
@@ -356,10 +374,10 @@ __device__ double step_error(int m, const double* d, const double* Q, double bet
 
 // One block (one warp) per batch column: eigendecomposition of T_b and the
 // largest s <= s_target whose error estimate is <= tol.
-__global__ void k_tridiag_eig(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
-                              const double* __restrict__ beta_last_arr, double zr, double zi, double s_target,
-                              double tol, double* __restrict__ theta, double* __restrict__ Qout,
-                              double* __restrict__ sb, int* status) {
+__device__ void tridiag_eig_block(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
+                                  const double* __restrict__ beta_last_arr, double zr, double zi, double s_target,
+                                  double tol, double* __restrict__ theta, double* __restrict__ Qout,
+                                  double* __restrict__ sb, int* status) {
   extern __shared__ double smd[];
   double* Q = smd;
   double* d = Q + m * m;
@@ -399,6 +417,13 @@ __global__ void k_tridiag_eig(int m, int B, const double* __restrict__ alpha, co
   if (lane == 0) sb[b] = s;
 }
 
+__global__ void k_tridiag_eig(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
+                              const double* __restrict__ beta_last_arr, double zr, double zi, double s_target,
+                              double tol, double* __restrict__ theta, double* __restrict__ Qout,
+                              double* __restrict__ sb, int* status) {
+  tridiag_eig_block(m, B, alpha, beta, beta_last_arr, zr, zi, s_target, tol, theta, Qout, sb, status);
+}
+
 __global__ void k_step_min(int B, const double* __restrict__ sb, double* __restrict__ sacc) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = sb[0];
@@ -432,6 +457,146 @@ __global__ void k_tridiag_coef(int m, int B, const double* __restrict__ theta, c
     const double b0 = beta0[b];
     c[k * B + b] = make_double2(b0 * re, b0 * im);
   }
+}
+
+// ---------------------------------------------------------------- device-driven evolution
+// Kernels of the evolution graph (expmv_chain): they read z, tol and the vectors from the
+// job record and keep the step state in DevCtl; single-thread kernels set the graph's
+// conditional handles (one thread each: concurrent sets would race).
+constexpr int kMaxSegs = 64;
+struct IfHandles {
+  cudaGraphConditionalHandle h[kMaxSegs];
+  int n;
+};
+
+__global__ void k_set_job(ExpJob* job, double zr, double zi, double tol, const void* in, void* out) {
+  job->zr = zr;
+  job->zi = zi;
+  job->tol = tol;
+  job->in = in;
+  job->out = out;
+}
+
+// n16 16-byte units: dir 0 copies the job's input into w, dir 1 w into the job's output
+__global__ void k_job_copy(const ExpJob* job, uint4* w, int64_t n16, int dir) {
+  const uint4* src = dir == 0 ? static_cast<const uint4*>(job->in) : w;
+  uint4* dst = dir == 0 ? w : static_cast<uint4*>(job->out);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n16; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+__global__ void k_job_begin(const ExpJob* job, DevCtl* ctl, cudaGraphConditionalHandle h_loop) {
+  ctl->s_rem = 1.0;
+  ctl->s_done = 0.0;
+  ctl->jsteps = 0;
+  cudaGraphSetConditional(h_loop, (job->zr != 0.0 || job->zi != 0.0) ? 1u : 0u);
+}
+
+__global__ void k_reset_ifs(IfHandles hs) {
+  for (int k = 0; k < hs.n; ++k) cudaGraphSetConditional(hs.h[k], 0u);
+}
+
+__global__ void k_tridiag_eig_dev(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
+                                  const double* __restrict__ beta_last_arr, const ExpJob* __restrict__ job,
+                                  const DevCtl* __restrict__ ctl, double* __restrict__ theta,
+                                  double* __restrict__ Qout, double* __restrict__ sb, int* status) {
+  tridiag_eig_block(m, B, alpha, beta, beta_last_arr, job->zr, job->zi, ctl->s_rem, job->tol, theta, Qout, sb,
+                    status);
+}
+
+// After the check that ends Lanczos segment [.., j1): converged when the accepted step covers
+// what remains (or the basis is full, or an error bit is set); the next segment's IF handle
+// is set accordingly.  Adds the segment's matvecs and kernel launches to the counters.
+__global__ void k_decide(DevCtl* ctl, int j1, int last, const int* __restrict__ st_ws,
+                         const int* __restrict__ st_apply, const double* __restrict__ sacc,
+                         cudaGraphConditionalHandle h_next, int has_next, long long seg_applies,
+                         long long seg_launches, long long mv_rows, long long mv_tiled, long long mv_coset) {
+  ctl->applies += seg_applies;
+  ctl->launches += seg_launches;
+  ctl->mv[0] += mv_rows;
+  ctl->mv[1] += mv_tiled;
+  ctl->mv[2] += mv_coset;
+  int e = 0;
+  if (st_ws[0] & 1) e |= 1;     // non-finite Lanczos scalar
+  if (st_ws[0] & 2) e |= 2;     // tridiagonal eigensolver did not converge
+  if (st_apply[0] & 4) e |= 4;  // a bounded wait of a matvec gave up
+  ctl->err |= e;
+  const bool conv = last || e != 0 || *sacc >= ctl->s_rem;
+  if (conv) ctl->m_eff = j1;
+  if (has_next) cudaGraphSetConditional(h_next, conv ? 0u : 1u);
+}
+
+// The accepted step of the basis, decided as expmv_T decides it for one output at fraction 1:
+// the output is combined from this basis when the step reaches it (within 1e-13) or covers
+// what remains; otherwise the basis' end state restarts the next one.
+__global__ void k_finalize(DevCtl* ctl, const double* __restrict__ sacc) {
+  const double s_acc = fmin(*sacc, ctl->s_rem);
+  if (!(s_acc > 1e-13 * ctl->s_rem) && !(s_acc >= ctl->s_rem)) ctl->err |= 8;  // step collapsed
+  const bool final_basis = s_acc >= ctl->s_rem;
+  const bool covered = final_basis || 1.0 <= ctl->s_done + s_acc * (1.0 + 1e-13);
+  ctl->s_acc = s_acc;
+  ctl->ds = covered ? (final_basis ? s_acc : fmin(1.0 - ctl->s_done, s_acc)) : s_acc;
+  ctl->done = covered ? 1 : 0;
+}
+
+__global__ void k_tridiag_coef_dev(int B, const double* __restrict__ theta, const double* __restrict__ Q,
+                                   const double* __restrict__ beta0, const ExpJob* __restrict__ job,
+                                   const DevCtl* __restrict__ ctl, double2* __restrict__ c) {
+  __shared__ double2 fg[SYK_MAX_KRYLOV];
+  const int m = ctl->m_eff;
+  const double s = ctl->ds, zr = job->zr, zi = job->zi;
+  const int b = blockIdx.x;
+  const int k = threadIdx.x;
+  const double* Qb = Q + (size_t)b * m * m;
+  if (k < m) {
+    const double2 f = cexp_scaled(s, zr, zi, theta[k * B + b]);
+    const double g = Qb[k];
+    fg[k] = make_double2(f.x * g, f.y * g);
+  }
+  __syncthreads();
+  if (k < m) {
+    double re = 0.0, im = 0.0;
+    for (int l = 0; l < m; ++l) {
+      const double q = Qb[k * m + l];
+      re = fma(q, fg[l].x, re);
+      im = fma(q, fg[l].y, im);
+    }
+    const double b0 = beta0[b];
+    c[k * B + b] = make_double2(b0 * re, b0 * im);
+  }
+}
+
+// out = sum_{k < m_eff} c_k v_k (m_eff from the control block)
+template <typename R>
+__global__ void k_combine_dev(const DevCtl* __restrict__ ctl, const typename CT<R>::T* __restrict__ V, size_t vs,
+                              const double2* __restrict__ c, const double* __restrict__ sc,
+                              typename CT<R>::T* __restrict__ out, int64_t total, int B) {
+  using C = typename CT<R>::T;
+  const int nk = ctl->m_eff;
+  const int b = threadIdx.x % B;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    C x = make_c<R>(R(0), R(0));
+    for (int k = 0; k < nk; ++k) {
+      const double2 ck = c[k * B + b];
+      const double f = sc[k * B + b];
+      cmac(x, R(ck.x * f), R(ck.y * f), V[(size_t)k * vs + e]);
+    }
+    out[e] = x;
+  }
+}
+
+// End of a Krylov basis: advance by the accepted step; loop while some of z remains.
+__global__ void k_advance(DevCtl* ctl, cudaGraphConditionalHandle h_loop, long long tail_launches) {
+  if (ctl->done) {
+    ctl->s_rem = 0.0;
+  } else {
+    ctl->s_done += ctl->s_acc;
+    ctl->s_rem -= ctl->s_acc;
+  }
+  ctl->bases += 1;
+  ctl->launches += tail_launches;
+  if (++ctl->jsteps > 100000) ctl->err |= 16;
+  cudaGraphSetConditional(h_loop, (ctl->s_rem > 0.0 && ctl->err == 0) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- launch helpers
@@ -515,8 +680,8 @@ int lanczos_step(const ApplyParams& P, int dtype, KrylovWS& ws, int j, int orth,
       Ops<R>::update(ws, 0, j + 1, ws.h1, ws.w, next, ws.npart, st);
     }
   }
-  k_lanczos_scalars<<<(int(B) + 127) / 128, 128, 0, st>>>(j, int(B), ws.G, ws.h1, two_pass ? ws.h2 : nullptr,
-                                                           ws.npart, ws.alpha, ws.beta, ws.inv, ws.sc, ws.status, bt);
+  k_lanczos_scalars<<<(int(B) + 7) / 8, 256, 0, st>>>(j, int(B), ws.G, ws.h1, two_pass ? ws.h2 : nullptr, ws.npart,
+                                                       ws.alpha, ws.beta, ws.inv, ws.sc, ws.status, bt);
   count_launch();
   SYK_CUDA_CHECK(cudaGetLastError());
   return SYK_OK;
@@ -558,6 +723,7 @@ size_t krylov_ws_bytes(int64_t D, int dtype, int m, int64_t B) {
   s += align_up(sizeof(double) * (m + 1) * B);                // sc
   s += align_up(sizeof(double2) * size_t(ep_capacity(D)) * B);  // ep_part
   s += align_up(sizeof(int));                                 // ep_nblk
+  s += align_up(sizeof(ExpJob)) + align_up(sizeof(DevCtl));   // job, ctl
   return s;
 }
 
@@ -604,6 +770,8 @@ int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype
   ws->ep_cap = ep_capacity(D);
   ws->ep_part = (double2*)take(sizeof(double2) * size_t(ws->ep_cap) * B);
   ws->ep_nblk = (int*)take(sizeof(int));
+  ws->job = (ExpJob*)take(sizeof(ExpJob));
+  ws->ctl = (DevCtl*)take(sizeof(DevCtl));
   return SYK_OK;
 }
 
@@ -705,6 +873,18 @@ int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int
   return SYK_OK;
 }
 
+// Convergence of a sub-step is checked after 4 vectors and then every `every` vectors.  A
+// check (eigensolve of T, ~0.4 ms) against the matvecs it can save: with c = check / matvec
+// cost, checking every k vectors of a basis that converges after ~m/2 vectors costs m/(2k)
+// checks plus ~k/2 matvecs of overshoot, least at k = sqrt(m c / 2).  The matvec cost is
+// modelled from its work (8 nnz B flop at ~20 TFLOP/s for complex64, ~4.4 for complex128,
+// plus 10 us); large states come out at every 2 vectors, N = 32 with 8 states at 6, N <= 28 at 16.
+int check_every(const ApplyParams& P, int dtype, int64_t D, int64_t B, int m) {
+  const double nnz = double(D) * double(P.n4 + P.n2 + 1);
+  const double apply_ms = 0.01 + 8.0 * nnz * double(B) / (dtype == SYK_C64 ? 2.0e10 : 4.4e9);
+  return std::max(2, std::min(16, int(std::lround(std::sqrt(0.5 * double(m) * 0.4 / apply_ms)))));
+}
+
 // outs[k] = e^{fr[k] z H} psi for 0 < fr[0] < ... < fr[nf-1]: the step to fr[nf-1] is split
 // into Krylov bases as the error estimate allows, and each output is combined from the basis
 // whose step covers its fraction.  Restarts pass through outs[nf-1], written last.
@@ -719,10 +899,7 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
   // reaches; complex128 vectors get the second pass ("twice is enough")
   const bool two_pass = dtype == SYK_C128;
   const int orth = lanczos_orth(dtype);
-  // Convergence of the sub-step is checked after 4 vectors and then every `every` vectors: a
-  // check (eigensolve of T + one host read) costs far less than a matvec once the state is
-  // large, so large states are checked every 2 vectors, small ones every 8.
-  const int every = (double(ws.D) * double(B) >= double(1 << 18)) ? 2 : 8;
+  const int every = check_every(P, dtype, ws.D, B, m);
   const double zr = z.real(), zi = z.imag();
   int* hstat = static_cast<int*>(ws.host_stage ? ws.host_stage : pinned_scratch(64));
   double* hs = reinterpret_cast<double*>(hstat + 4);
@@ -868,6 +1045,280 @@ int expmv_points(const ApplyParams& P, int dtype, std::complex<double> z, const 
   }
   return dtype == SYK_C64 ? expmv_T<float>(P, dtype, z, psi, fr, nf, outs, tol, ws, st, nullptr)
                           : expmv_T<double>(P, dtype, z, psi, fr, nf, outs, tol, ws, st, nullptr);
+}
+
+// ---------------------------------------------------------------- device-driven chain
+namespace {
+
+struct DevKey {
+  const void* V;
+  const void* tab;
+  int sector, dtype;
+  int64_t B, D;
+  int m, orth, every;
+  uint64_t epoch;
+  bool operator<(const DevKey& o) const {
+    return std::tie(V, tab, sector, dtype, B, D, m, orth, every, epoch) <
+           std::tie(o.V, o.tab, o.sector, o.dtype, o.B, o.D, o.m, o.orth, o.every, o.epoch);
+  }
+};
+struct DevCache {
+  std::map<DevKey, cudaGraphExec_t> graphs;
+  cudaStream_t cap = nullptr;
+  ~DevCache() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  }
+};
+thread_local DevCache t_dev;
+
+std::vector<cudaGraphNode_t> capture_frontier(cudaStream_t s) {
+  cudaStreamCaptureStatus stt;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s, &stt, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess) return {};
+  return std::vector<cudaGraphNode_t>(deps, deps + nd);
+}
+
+// Builds the graph of one evolution out = e^{zH} in on workspace ws (z, tol, in, out from
+// ws.job; step state in ws.ctl):
+//   copy in -> w; WHILE (some of z remains) {
+//     v_0 = w / |w|; Lanczos segment [0, 4); check; then for each later segment
+//     IF (not converged) { segment; check }   (sequential IF nodes, reset each iteration)
+//     coefficients of the accepted step; w = V c; advance }
+//   copy w -> out.
+// The segments and checks are exactly expmv_T's, so results equal the host-driven path's.
+template <typename R>
+int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, bool two_pass, int every, double bt,
+                    cudaStream_t st, cudaGraphExec_t* out) {
+  const int64_t B = ws.B;
+  const int m = ws.m;
+  if (!t_dev.cap) SYK_CUDA_CHECK(cudaStreamCreateWithFlags(&t_dev.cap, cudaStreamNonBlocking));
+  cudaStream_t cs = t_dev.cap;  // capture only: nothing executes on it
+  // Lazily built chunk lists and coset layouts, kernel attributes: one eager matvec first, on
+  // the caller's stream so that it is ordered after the chain's pending work on this workspace
+  // (its counts are dropped: it is set-up, not work of the evolution).
+  int64_t wl = 0, wa = 0, wk[kMvKinds];
+  capture_counts_begin();
+  const int wrc = launch_apply_H(P, dtype, ws.vec(0), ws.w, B, st);
+  capture_counts_end(&wl, &wa, wk);
+  SYK_TRY(wrc);
+  // segment ends: after 4 vectors, then at multiples of `every`, and at m (as in expmv_T)
+  std::vector<int> j1s;
+  for (int j0 = 0; j0 < m;) {
+    int j1 = j0 + 1;
+    while (!(j1 == m || j1 == 4 || (j1 > 4 && j1 % every == 0))) ++j1;
+    j1s.push_back(j1);
+    j0 = j1;
+  }
+  const int nseg = int(j1s.size());
+  if (nseg > kMaxSegs) {
+    set_error("expmv graph: %d segments exceed %d", nseg, kMaxSegs);
+    return SYK_EINVAL;
+  }
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  const int64_t n16 = int64_t(ws.vec_bytes() / 16);
+  const int cg = std::min<int64_t>((n16 + 255) / 256, 4 * sm_count());
+  cudaGraph_t g = nullptr;
+  SYK_CUDA_CHECK(cudaGraphCreate(&g, 0));
+  int rc = SYK_OK;
+  auto fail = [&](cudaError_t e, const char* what) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamCaptureStatus stt;
+    if (cudaStreamIsCapturing(cs, &stt) == cudaSuccess && stt != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(cs, &junk);
+    cudaGetLastError();
+    set_error("expmv graph: %s: %s", what, cudaGetErrorString(e));
+    return SYK_ECUDA;
+  };
+#define DEV_CK(expr, what)                 \
+  do {                                     \
+    cudaError_t e_ = (expr);               \
+    if (e_ != cudaSuccess) {               \
+      rc = fail(e_, what);                 \
+      cudaGraphDestroy(g);                 \
+      return rc;                           \
+    }                                      \
+  } while (0)
+  cudaGraphConditionalHandle hloop;
+  DEV_CK(cudaGraphConditionalHandleCreate(&hloop, g, 0, 0), "loop handle");
+  // prologue: w = in, loop condition
+  DEV_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode), "capture");
+  capture_counts_begin();
+  k_job_copy<<<cg, 256, 0, cs>>>(ws.job, reinterpret_cast<uint4*>(ws.w), n16, 0);
+  k_job_begin<<<1, 1, 0, cs>>>(ws.job, ws.ctl, hloop);
+  std::vector<cudaGraphNode_t> fr = capture_frontier(cs);
+  DEV_CK(cudaStreamEndCapture(cs, &g), "end capture");
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hloop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  DEV_CK(cudaGraphAddNode(&wnode, g, fr.data(), nullptr, fr.size(), &wp), "while node");
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  IfHandles ifs = {};
+  ifs.n = nseg - 1;
+  for (int k = 0; k < ifs.n; ++k) DEV_CK(cudaGraphConditionalHandleCreate(&ifs.h[k], body, 0, 0), "if handle");
+  // one segment of Lanczos steps [j0, j1) and its convergence check, captured on cs
+  auto segment = [&](int k, int j0, int j1) -> int {
+    int64_t l0 = 0, a0 = 0, kinds[kMvKinds];
+    capture_counts_begin();  // the segment's own tallies (launches and matvecs per execution)
+    for (int j = j0; j < j1; ++j) SYK_TRY(lanczos_step<R>(P, dtype, ws, j, orth, two_pass, bt, cs));
+    capture_counts_end(&l0, &a0, kinds);
+    capture_counts_begin();  // keep counting captured launches away from the global counters
+    const int mm = j1;
+    const size_t smem = sizeof(double) * (size_t(mm) * mm + 2 * mm + 2);
+    k_tridiag_eig_dev<<<int(B), 32, smem, cs>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j1 - 1) * B, ws.job,
+                                                ws.ctl, ws.theta, ws.Q, ws.sb, ws.status);
+    k_step_min<<<1, 32, 0, cs>>>(int(B), ws.sb, ws.sacc);
+    const bool has_next = k + 1 < nseg;
+    k_decide<<<1, 1, 0, cs>>>(ws.ctl, j1, j1 == m ? 1 : 0, ws.status, P.status, ws.sacc,
+                              has_next ? ifs.h[k] : cudaGraphConditionalHandle(0), has_next ? 1 : 0, a0, l0 + 3,
+                              kinds[kMvRows], kinds[kMvTiled], kinds[kMvCoset]);
+    SYK_CUDA_CHECK(cudaGetLastError());
+    return SYK_OK;
+  };
+  // body head: reset the IF handles, v_0 = w / |w|, first segment
+  DEV_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode), "capture body");
+  k_reset_ifs<<<1, 1, 0, cs>>>(ifs);
+  Ops<R>::dots(ws, 1, ws.w, 0, ws.w, cs);
+  reduce_parts(ws, 1, ws.h1, cs);
+  k_norm_init<<<(int(B) + 127) / 128, 128, 0, cs>>>(int(B), ws.h1, ws.beta0, ws.inv, ws.sc, ws.status);
+  Ops<R>::scale(ws, ws.w, ws.vec(0), ws.inv, cs);
+  rc = segment(0, 0, j1s[0]);
+  fr = capture_frontier(cs);
+  {
+    cudaGraph_t tmp = body;
+    DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture body");
+  }
+  if (rc != SYK_OK) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  for (int k = 1; k < nseg; ++k) {
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = ifs.h[k - 1];
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    DEV_CK(cudaGraphAddNode(&inode, body, fr.data(), nullptr, fr.size(), &ip), "if node");
+    cudaGraph_t ib = ip.conditional.phGraph_out[0];
+    DEV_CK(cudaStreamBeginCaptureToGraph(cs, ib, nullptr, nullptr, 0, mode), "capture if");
+    rc = segment(k, j1s[k - 1], j1s[k]);
+    {
+      cudaGraph_t tmp = ib;
+      DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture if");
+    }
+    if (rc != SYK_OK) {
+      cudaGraphDestroy(g);
+      return rc;
+    }
+    fr = {inode};
+  }
+  // body tail: the accepted step's coefficients, w = V c, advance
+  DEV_CK(cudaStreamBeginCaptureToGraph(cs, body, fr.data(), nullptr, fr.size(), mode), "capture tail");
+  k_finalize<<<1, 1, 0, cs>>>(ws.ctl, ws.sacc);
+  k_tridiag_coef_dev<<<int(B), 64, 0, cs>>>(int(B), ws.theta, ws.Q, ws.beta0, ws.job, ws.ctl, ws.c);
+  k_combine_dev<R><<<ws.G, ws.bdim, 0, cs>>>(ws.ctl, (const typename CT<R>::T*)ws.V, size_t(ws.D * B), ws.c, ws.sc,
+                                             (typename CT<R>::T*)ws.w, ws.D * B, int(B));
+  // per basis: reset, the 4 kernels of v_0, finalize, coefficients, combine, advance
+  k_advance<<<1, 1, 0, cs>>>(ws.ctl, hloop, 9);
+  {
+    cudaGraph_t tmp = body;
+    DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture tail");
+  }
+  // epilogue: out = w
+  DEV_CK(cudaStreamBeginCaptureToGraph(cs, g, &wnode, nullptr, 1, mode), "capture epilogue");
+  k_job_copy<<<cg, 256, 0, cs>>>(ws.job, reinterpret_cast<uint4*>(ws.w), n16, 1);
+  {
+    cudaGraph_t tmp = g;
+    DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture epilogue");
+  }
+  int64_t l0 = 0, a0 = 0, kinds[kMvKinds];
+  capture_counts_end(&l0, &a0, kinds);
+  cudaGraphExec_t exec = nullptr;
+  DEV_CK(cudaGraphInstantiate(&exec, g, 0), "instantiate");
+  cudaGraphDestroy(g);
+  *out = exec;
+#undef DEV_CK
+  return SYK_OK;
+}
+
+}  // namespace
+
+int chain_begin(KrylovWS& ws, cudaStream_t st) {
+  SYK_CUDA_CHECK(cudaMemsetAsync(ws.ctl, 0, sizeof(DevCtl), st));
+  SYK_CUDA_CHECK(cudaMemsetAsync(ws.status, 0, sizeof(int) * 4, st));
+  return SYK_OK;
+}
+
+int expmv_chain(const ApplyParams& P_in, int dtype, std::complex<double> z, const void* in, void* out, int64_t B,
+                double tol, KrylovWS& ws, cudaStream_t st) {
+  if (P_in.no_alloc || !graphs_enabled() || prof_enabled())
+    return expmv_impl(P_in, dtype, z, in, out, B, tol, ws, st, nullptr);
+  if (ws.B != B || ws.D != P_in.D || ws.dtype != dtype) {
+    set_error("expmv: workspace shape mismatch");
+    return SYK_EINVAL;
+  }
+  if (!(tol > 0.0)) {
+    set_error("expmv: tol must be > 0");
+    return SYK_EINVAL;
+  }
+  const ApplyParams P = ws.with_split(P_in);
+  const int orth = lanczos_orth(dtype);
+  const int every = check_every(P, dtype, ws.D, B, ws.m);
+  const DevKey key{ws.V, P.m4_tab, P.sector, dtype, B, P.D, ws.m, orth, every, graph_epoch()};
+  auto it = t_dev.graphs.find(key);
+  if (it == t_dev.graphs.end()) {
+    if (t_dev.graphs.size() > 256) {
+      for (auto& kv : t_dev.graphs) cudaGraphExecDestroy(kv.second);
+      t_dev.graphs.clear();
+    }
+    const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
+    cudaGraphExec_t exec = nullptr;
+    const int rc = dtype == SYK_C64 ? build_dev_graph<float>(P, dtype, ws, orth, false, every, bt, st, &exec)
+                                    : build_dev_graph<double>(P, dtype, ws, orth, true, every, bt, st, &exec);
+    if (rc != SYK_OK) return rc;
+    it = t_dev.graphs.emplace(key, exec).first;
+  }
+  k_set_job<<<1, 1, 0, st>>>(ws.job, z.real(), z.imag(), tol, in, out);
+  SYK_CUDA_CHECK(cudaGetLastError());
+  SYK_CUDA_CHECK(cudaGraphLaunch(it->second, st));
+  count_launch(4);  // set_job, and the graph's copy in, loop set-up and copy out
+  return SYK_OK;
+}
+
+int chain_end(KrylovWS& ws, cudaStream_t st) {
+  DevCtl h;
+  SYK_CUDA_CHECK(cudaMemcpyAsync(&h, ws.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+  SYK_CUDA_CHECK(cudaStreamSynchronize(st));
+  count_applies(h.applies);
+  count_bases(h.bases);
+  count_launch(h.launches);
+  const int64_t mv[kMvKinds] = {h.mv[0], h.mv[1], h.mv[2]};
+  count_matvec_replay(mv);
+  if (h.err & 4) {
+    set_error("apply_H: a bounded wait for a staged tile gave up");
+    return SYK_ETIMEOUT;
+  }
+  if (h.err & 1) {
+    set_error("expmv: non-finite Lanczos scalar");
+    return SYK_ENUMERIC;
+  }
+  if (h.err & 2) {
+    set_error("expmv: tridiagonal eigensolver did not converge");
+    return SYK_ENUMERIC;
+  }
+  if (h.err & 8) {
+    set_error("expmv: Krylov step collapsed; raise krylov_dim or tol");
+    return SYK_ENUMERIC;
+  }
+  if (h.err & 16) {
+    set_error("expmv: more than 100000 Krylov steps");
+    return SYK_ENUMERIC;
+  }
+  return SYK_OK;
 }
 
 namespace {

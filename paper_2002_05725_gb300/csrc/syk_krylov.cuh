@@ -7,6 +7,20 @@
 
 namespace syk {
 
+// Device-side control of an evolution run as one CUDA graph (see expmv_chain): the job (z,
+// tol, input and output vectors), the step state, error bits and work counters.
+struct ExpJob {
+  double zr, zi, tol;
+  const void* in;
+  void* out;
+};
+struct DevCtl {
+  double s_rem, s_done, ds, s_acc;
+  int m_eff, err, jsteps, done;
+  long long bases, applies, launches;
+  long long mv[3];  // matvec launches by kernel family (rows, tiled, coset)
+};
+
 // Device scratch of one Lanczos process over a batch of B states of dimension D.
 struct KrylovWS {
   int m = 0;            // maximum Krylov dimension
@@ -37,6 +51,8 @@ struct KrylovWS {
   double2* ep_part = nullptr;  // per-CTA partial dots of the matvec epilogue (ep_cap * B)
   int* ep_nblk = nullptr;
   int64_t ep_cap = 0;
+  ExpJob* job = nullptr;     // the evolution a device-driven graph runs next
+  DevCtl* ctl = nullptr;
   void* host_stage = nullptr;  // host buffer (>= 64 B) for status reads; NULL: pinned scratch
   size_t vec_bytes() const { return size_t(D) * B * dtype_size(dtype); }
   char* vec(int k) const { return V + size_t(k) * vec_bytes(); }
@@ -63,6 +79,17 @@ int krylov_ws_carve(KrylovWS* ws, void* base, size_t bytes, int64_t D, int dtype
 // out = e^{z H} psi (see syk_expmv).  psi and out may alias.
 int expmv_impl(const ApplyParams& P, int dtype, std::complex<double> z, const void* psi, void* out,
                int64_t B, double tol, KrylovWS& ws, cudaStream_t st, int* nsteps);
+
+// The evolutions of a correlator chain: out = e^{zH} in (in and out may alias), as expmv_impl.
+// With CUDA graphs enabled and profiling off, each is one launch of a graph that runs the
+// whole Krylov loop with its step control on the device (conditional WHILE and IF nodes):
+// the host only enqueues, with no synchronisation until the chain ends.  chain_begin clears
+// the device-side error bits and counters; chain_end (called after the caller has
+// synchronised the stream) reports the first device-side error and adds the counters.
+int chain_begin(KrylovWS& ws, cudaStream_t st);
+int expmv_chain(const ApplyParams& P, int dtype, std::complex<double> z, const void* in, void* out, int64_t B,
+                double tol, KrylovWS& ws, cudaStream_t st);
+int chain_end(KrylovWS& ws, cudaStream_t st);
 
 // outs[k] = e^{fr[k] z H} psi for increasing fractions 0 < fr[0] < ... < fr[nf-1], each output
 // combined from the Krylov basis whose step covers it (no extra matvecs per output).  psi may

@@ -52,6 +52,14 @@ CHILD = textwrap.dedent("""
         except syk.SykError as e:
             assert "code -5" in str(e), str(e)
         syk.syk_status(terms, reset=True)
+        # a correlator chain, its evolutions run as graphs with the step control on the device:
+        # the timeout surfaces when the chain ends
+        try:
+            syk.syk_otoc(terms, 1.0, 0, 1, [0.0, 0.5], x, krylov_dim=20, tol=1e-7)
+            raise AssertionError("syk_otoc did not report the timeout")
+        except syk.SykError as e:
+            assert "code -5" in str(e), str(e)
+        syk.syk_status(terms, reset=True)
     else:
         assert st == syk.SYK_OK, st
         assert err < 1e-5, err
