@@ -55,6 +55,9 @@ def parse():
                     help="mixed-N batched workload (N 20..40, beta J 1/3/10, 8 states per draw)")
     ap.add_argument("--draws", type=int, default=1, help="coupling draws per (N, beta) in --batched mode")
     ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--batched-Ns", default="20,24,28,32,36,40", help="sizes of the --batched workload")
+    ap.add_argument("--graphs", default="segments", choices=["off", "segments", "device"],
+                    help="launch mode of the Krylov evolutions of the --batched workload (syk_use_graphs 0/1/2)")
     ap.add_argument("--grad", action="store_true",
                     help="gradient workload: dF~(t*)/dJ for all couplings and dF~/dbeta at N=28, beta J=5, "
                          "t*=5, about 200 quadrature sub-intervals, 8 states, c64 and c128")
@@ -168,7 +171,7 @@ def applies_model(N, beta, times, m=40, tol=1e-7):
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, index):
         self.index = index
@@ -198,7 +201,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.th.join(timeout=2)
-        sm, smax, reasons = [], 0.0, set()
+        sm, smax, reasons, util = [], 0.0, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -211,13 +214,20 @@ class ClockSampler:
                 smax = max(smax, float(f[2]))
             except ValueError:
                 continue
+            try:
+                util.append(float(f[9]))
+            except (IndexError, ValueError):
+                pass
             for name, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        if util:
+            # nvidia-smi utilization.gpu: percent of the sample period in which a kernel ran
+            out["gpu_busy_pct_mean"] = statistics.fmean(util)
+        return out
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -505,7 +515,8 @@ def run_batched(a, rank, world, local_rank, draws):
     torch.cuda.set_device(local_rank)
     syk.load()
     times = time_grid(a.npts, a.tmax)
-    Ns, betas = [20, 24, 28, 32, 36, 40], [1.0, 3.0, 10.0]
+    Ns, betas = [int(v) for v in a.batched_Ns.split(",")], [1.0, 3.0, 10.0]
+    syk.syk_use_graphs({"off": 0, "segments": 1, "device": 2}[a.graphs])
     items = []
     for d in range(draws):
         for N in Ns:
@@ -518,19 +529,26 @@ def run_batched(a, rank, world, local_rank, draws):
     syk.syk_otoc_batch(items[:len(Ns)], 0, 1, [0.0, 1.0], dtype=syk.SYK_C64, nworkers=a.workers)  # warm-up/tune
     syk.syk_counters(reset=True)
     torch.cuda.synchronize()
+    clk = ClockSampler(local_rank)
+    clk.start()
     t0 = time.perf_counter()
     out = syk.syk_otoc_batch(items, 0, 1, times, dtype=syk.SYK_C64, krylov_dim=a.krylov, tol=a.tol,
                              nworkers=a.workers)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    clocks = clk.stop()
     cnt = syk.syk_counters(reset=True)
+    syk.syk_use_graphs(True)
     curves = 8 * len(items)
     return {"metric": "OTOC curves/hour, mixed-N batch", "value": world * curves * 3600.0 / wall,
             "unit": "curves/hour", "wall_s": wall, "dtype": "c64",
             "config": {"workload": f"{draws} draw(s) x N in {Ns} x beta J in {betas}, 8 states each, "
                                    f"F~ at t=0 and {a.npts} points to t={a.tmax:g}, Krylov {a.krylov}, "
                                    f"tol {a.tol:g}, {a.workers} host workers / streams",
-                       "items": len(items), "curves": curves},
+                       "items": len(items), "curves": curves,
+                       "evolutions": {"off": "host-driven, direct launches", "segments": "host-driven, segment graphs",
+                                      "device": "device-driven graphs"}[a.graphs]},
+            "clocks": clocks,
             "gpu_launches": cnt["launches"], "h_applies": cnt["h_applies"],
             "result_check": {"Ftilde_t0_all_one": bool(all(np.allclose(F[0] / F[0], 1) for F in out))}}
 

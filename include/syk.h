@@ -345,10 +345,16 @@ int syk_matvec_launches(int64_t* rows, int64_t* tiled, int64_t* coset, int reset
  * the device).  Reading returns launches and total milliseconds; reset != 0
  * zeroes them. */
 int syk_profile_enable(int on);
-/* syk_use_graphs -- on (default) / off: replay the Lanczos iterations between two
- * convergence checks as captured CUDA graphs (per host thread, per workspace;
- * graphs are rebuilt after term sets are freed or tile shapes retuned).  Graphs
- * are not used while profiling is enabled. */
+/* syk_use_graphs -- how the Krylov evolutions are launched.  0: every kernel directly, with
+ * one host read per convergence check.  1 (default): the same, but the Lanczos iterations
+ * between two convergence checks are replayed as captured CUDA graphs (per host thread, per
+ * workspace; rebuilt after term sets are freed or tile shapes retuned).  2: each evolution of a
+ * correlator chain (syk_correlator_G, syk_otoc, syk_otoc_split, syk_correlator_G_imag, the
+ * batch) is one launch of a graph that runs the whole Krylov loop with its step control on the
+ * device (conditional WHILE and IF nodes): the chain is enqueued without host
+ * synchronisation, with bit-identical results; the graph is built once per workspace, term
+ * set and sector, which costs more than it saves for a chain run only once (syk_expmv and
+ * the gradients stay host-driven).  Graphs are not used while profiling is enabled. */
 int syk_use_graphs(int on);
 int syk_profile_read(int64_t* launches, double* total_ms, int reset);
 

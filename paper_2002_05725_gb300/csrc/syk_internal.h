@@ -154,6 +154,7 @@ bool prof_enabled();
 uint64_t graph_epoch();  // changes whenever captured graphs may hold stale parameters
 void bump_graph_epoch();
 bool graphs_enabled();
+bool device_chains_enabled();  // syk_use_graphs(2)
 
 // Arithmetic of the complex128 matvec: double-float (FP32 error-free transformations, the
 // default) or native FP64 (syk_c128_arith).

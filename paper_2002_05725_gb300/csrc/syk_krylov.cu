@@ -1255,7 +1255,7 @@ int chain_begin(KrylovWS& ws, cudaStream_t st) {
 
 int expmv_chain(const ApplyParams& P_in, int dtype, std::complex<double> z, const void* in, void* out, int64_t B,
                 double tol, KrylovWS& ws, cudaStream_t st) {
-  if (P_in.no_alloc || !graphs_enabled() || prof_enabled())
+  if (P_in.no_alloc || !device_chains_enabled() || prof_enabled())
     return expmv_impl(P_in, dtype, z, in, out, B, tol, ws, st, nullptr);
   if (ws.B != B || ws.D != P_in.D || ws.dtype != dtype) {
     set_error("expmv: workspace shape mismatch");

@@ -46,7 +46,7 @@ thread_local bool t_capturing = false;
 thread_local int64_t t_cap_launches = 0, t_cap_applies = 0;
 thread_local int64_t t_cap_mv[kMvKinds] = {};
 std::atomic<uint64_t> g_epoch{1};
-std::atomic<bool> g_graphs{true};
+std::atomic<int> g_graphs{1};  // 0 off, 1 segment graphs, 2 device-driven evolutions
 
 void count_applies(int64_t states) {
   if (t_capturing) t_cap_applies += states;
@@ -77,7 +77,8 @@ void capture_counts_end(int64_t* launches, int64_t* applies, int64_t* kinds) {
 }
 uint64_t graph_epoch() { return g_epoch.load(); }
 void bump_graph_epoch() { ++g_epoch; }
-bool graphs_enabled() { return g_graphs.load(); }
+bool graphs_enabled() { return g_graphs.load() != 0; }
+bool device_chains_enabled() { return g_graphs.load() == 2; }
 
 bool prof_enabled() {
   Prof& p = prof();
@@ -186,7 +187,11 @@ extern "C" int syk_matvec_launches(int64_t* rows, int64_t* tiled, int64_t* coset
 }
 
 extern "C" int syk_use_graphs(int on) {
-  syk::g_graphs = on != 0;
+  if (on < 0 || on > 2) {
+    syk::set_error("syk_use_graphs: mode must be 0, 1 or 2 (got %d)", on);
+    return SYK_EINVAL;
+  }
+  syk::g_graphs = on;
   syk::bump_graph_epoch();
   return SYK_OK;
 }

@@ -395,8 +395,12 @@ def syk_lowest_eigenvalues(terms: Terms, k: int, psi0, parity: int = 0, max_step
     return ev, rs, n.value
 
 
-def syk_use_graphs(on: bool = True):
-    _check(load().syk_use_graphs(int(on)), "syk_use_graphs")
+GRAPHS_OFF, GRAPHS_SEGMENTS, GRAPHS_DEVICE = 0, 1, 2
+
+
+def syk_use_graphs(mode=True):
+    """0 / False: direct launches; 1 / True: segment graphs (default); 2: device-driven evolutions."""
+    _check(load().syk_use_graphs(int(mode)), "syk_use_graphs")
 
 
 def syk_otoc_split(terms: Terms, beta: float, x, i: int, j: int, times, psi0, krylov_dim: int = 40,

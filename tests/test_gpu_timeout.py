@@ -52,14 +52,17 @@ CHILD = textwrap.dedent("""
         except syk.SykError as e:
             assert "code -5" in str(e), str(e)
         syk.syk_status(terms, reset=True)
-        # a correlator chain, its evolutions run as graphs with the step control on the device:
-        # the timeout surfaces when the chain ends
-        try:
-            syk.syk_otoc(terms, 1.0, 0, 1, [0.0, 0.5], x, krylov_dim=20, tol=1e-7)
-            raise AssertionError("syk_otoc did not report the timeout")
-        except syk.SykError as e:
-            assert "code -5" in str(e), str(e)
-        syk.syk_status(terms, reset=True)
+        # a correlator chain, host-driven and with the step control on the device (the timeout
+        # then surfaces when the chain ends)
+        for mode in (syk.GRAPHS_SEGMENTS, syk.GRAPHS_DEVICE):
+            syk.syk_use_graphs(mode)
+            try:
+                syk.syk_otoc(terms, 1.0, 0, 1, [0.0, 0.5], x, krylov_dim=20, tol=1e-7)
+                raise AssertionError("syk_otoc did not report the timeout")
+            except syk.SykError as e:
+                assert "code -5" in str(e), str(e)
+            syk.syk_status(terms, reset=True)
+        syk.syk_use_graphs(syk.GRAPHS_SEGMENTS)
     else:
         assert st == syk.SYK_OK, st
         assert err < 1e-5, err
