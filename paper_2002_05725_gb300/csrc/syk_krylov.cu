@@ -282,6 +282,24 @@ __global__ void k_lanczos_scalars(int j, int B, int G, const double2* __restrict
 // computes every Givens rotation (the scalar recurrence), all lanes apply it
 // to their rows of the accumulated eigenvector matrix Q (row-major m x m in
 // shared memory).  On return d holds the eigenvalues and T = Q diag(d) Q^T.
+// Givens rotation (c, s) with c x + s y = r, -s x + c y = 0; r^2 = x^2 + y^2 (the entries of
+// T are O(1) to O(10^2), so the squares neither overflow nor underflow) and one reciprocal
+// square root instead of a hypot and two divisions: the chain of dependent FP64 operations
+// of the bulge chase is the eigensolver's latency.
+__device__ __forceinline__ void givens(double x, double y, double& c, double& s, double& r) {
+  const double r2 = fma(x, x, y * y);
+  if (r2 > 0.0) {
+    const double ri = rsqrt(r2);
+    c = x * ri;
+    s = y * ri;
+    r = r2 * ri;
+  } else {
+    c = 1.0;
+    s = 0.0;
+    r = 0.0;
+  }
+}
+
 __device__ bool tridiag_eig_warp(int m, double* d, double* e, double* Q, double* rot) {
   const int lane = threadIdx.x & 31;
   for (int r = lane; r < m; r += 32)
@@ -312,8 +330,8 @@ __device__ bool tridiag_eig_warp(int m, double* d, double* e, double* Q, double*
     }
     for (int k = l; k < q; ++k) {
       if (lane == 0) {
-        const double r = hypot(x, y);
-        const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? y / r : 0.0;
+        double c, s, r;
+        givens(x, y, c, s, r);
         if (k > l) e[k - 1] = r;
         const double a = d[k], b = e[k], cc = d[k + 1];
         d[k] = c * c * a + 2.0 * c * s * b + s * s * cc;
@@ -341,6 +359,52 @@ __device__ bool tridiag_eig_warp(int m, double* d, double* e, double* Q, double*
   return ok;
 }
 
+// The same implicit QR, run by the calling thread alone, accumulating only rows 0 and m-1 of
+// Q (q0, qm): all the convergence check's error estimate needs, with no warp synchronisation
+// per rotation.  Same rotations as tridiag_eig_warp, so d ends up with the same eigenvalues.
+__device__ bool tridiag_eig_rows(int m, double* d, double* e, double* q0, double* qm) {
+  for (int c = 0; c < m; ++c) {
+    q0[c] = c == 0 ? 1.0 : 0.0;
+    qm[c] = c == m - 1 ? 1.0 : 0.0;
+  }
+  const double eps = 2.220446049250313e-16;
+  int q = m - 1;
+  int iter = 0;
+  while (q > 0) {
+    if (fabs(e[q - 1]) <= eps * (fabs(d[q - 1]) + fabs(d[q]))) {
+      --q;
+      continue;
+    }
+    if (++iter > 64 * m) return false;
+    int l = q - 1;
+    while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
+    const double dd = 0.5 * (d[q - 1] - d[q]);
+    const double ee = e[q - 1];
+    const double mu = d[q] - ee * ee / (dd + copysign(hypot(dd, ee), dd));
+    double x = d[l] - mu, y = e[l];
+    for (int k = l; k < q; ++k) {
+      double c, s, r;
+      givens(x, y, c, s, r);
+      if (k > l) e[k - 1] = r;
+      const double a = d[k], b = e[k], cc = d[k + 1];
+      d[k] = c * c * a + 2.0 * c * s * b + s * s * cc;
+      d[k + 1] = s * s * a - 2.0 * c * s * b + c * c * cc;
+      e[k] = c * s * (cc - a) + (c * c - s * s) * b;
+      if (k + 1 < q) {
+        y = s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+        x = e[k];
+      }
+      const double a0 = q0[k], b0 = q0[k + 1], am = qm[k], bm = qm[k + 1];
+      q0[k] = c * a0 + s * b0;
+      q0[k + 1] = -s * a0 + c * b0;
+      qm[k] = c * am + s * bm;
+      qm[k + 1] = -s * am + c * bm;
+    }
+  }
+  return true;
+}
+
 __device__ __forceinline__ double2 cexp_scaled(double s, double zr, double zi, double th) {
   const double mag = exp(s * zr * th);
   double sn, cs;
@@ -354,13 +418,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Saad's estimate of the relative error of the step s: beta_last |e_m^T e^{szT} e_1| / ||e^{szT} e_1||
-__device__ double step_error(int m, const double* d, const double* Q, double beta_last, double s, double zr, double zi) {
+// (q0, qm: rows 0 and m-1 of the eigenvector matrix)
+__device__ double step_error(int m, const double* d, const double* q0, const double* qm, double beta_last, double s,
+                             double zr, double zi) {
   if (beta_last == 0.0) return 0.0;
   const int lane = threadIdx.x & 31;
   double nr = 0.0, ni = 0.0, den = 0.0;
   for (int k = lane; k < m; k += 32) {
     const double2 f = cexp_scaled(s, zr, zi, d[k]);
-    const double g = Q[k], h = Q[(m - 1) * m + k];
+    const double g = q0[k], h = qm[k];
     nr += h * g * f.x;
     ni += h * g * f.y;
     den += (f.x * f.x + f.y * f.y) * g * g;
@@ -372,17 +438,29 @@ __device__ double step_error(int m, const double* d, const double* Q, double bet
   return beta_last * sqrt(nr * nr + ni * ni) / sqrt(den);
 }
 
-// One block (one warp) per batch column: eigendecomposition of T_b and the
-// largest s <= s_target whose error estimate is <= tol.
+// One block (one warp) per batch column: eigendecomposition of T_b and the largest
+// s <= s_target whose error estimate is <= tol.  FULL: the whole eigenvector matrix (for the
+// combination coefficients), written to Qout; otherwise only rows 0 and m-1 (a convergence
+// check), computed by lane 0 alone.  Shared memory: m^2 + 2m + 2 doubles (FULL) or 4m.
+template <bool FULL>
 __device__ void tridiag_eig_block(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
                                   const double* __restrict__ beta_last_arr, double zr, double zi, double s_target,
                                   double tol, double* __restrict__ theta, double* __restrict__ Qout,
                                   double* __restrict__ sb, int* status) {
   extern __shared__ double smd[];
-  double* Q = smd;
-  double* d = Q + m * m;
-  double* e = d + m;
-  double* rot = e + m;
+  double *Q, *d, *e, *q0, *qm;
+  if constexpr (FULL) {
+    Q = smd;
+    d = Q + m * m;
+    e = d + m;
+    q0 = Q;
+    qm = Q + (m - 1) * m;
+  } else {
+    d = smd;
+    e = d + m;
+    q0 = e + m;
+    qm = q0 + m;
+  }
   const int b = blockIdx.x;
   const int lane = threadIdx.x;
   for (int k = lane; k < m; k += 32) {
@@ -390,15 +468,23 @@ __device__ void tridiag_eig_block(int m, int B, const double* __restrict__ alpha
     e[k] = k + 1 < m ? beta[k * B + b] : 0.0;
   }
   __syncwarp();
-  const bool ok = tridiag_eig_warp(m, d, e, Q, rot);
+  bool ok;
+  if constexpr (FULL) {
+    ok = tridiag_eig_warp(m, d, e, Q, e + m);
+  } else {
+    ok = true;
+    if (lane == 0) ok = tridiag_eig_rows(m, d, e, q0, qm);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+  }
   if (!ok && lane == 0) atomicOr(status, 2);
   const double bl = beta_last_arr ? beta_last_arr[b] : 0.0;
   double s = s_target;
-  if (step_error(m, d, Q, bl, s, zr, zi) > tol) {
+  if (step_error(m, d, q0, qm, bl, s, zr, zi) > tol) {
     double lo = 0.0, hi = s;
     s *= 0.5;
     int it = 0;
-    while (step_error(m, d, Q, bl, s, zr, zi) > tol && it < 80) {
+    while (step_error(m, d, q0, qm, bl, s, zr, zi) > tol && it < 80) {
       hi = s;
       s *= 0.5;
       ++it;
@@ -406,22 +492,28 @@ __device__ void tridiag_eig_block(int m, int B, const double* __restrict__ alpha
     lo = s;
     for (int k = 0; k < 24; ++k) {  // largest admissible step within [lo, hi)
       const double mid = 0.5 * (lo + hi);
-      if (step_error(m, d, Q, bl, mid, zr, zi) <= tol) lo = mid;
+      if (step_error(m, d, q0, qm, bl, mid, zr, zi) <= tol) lo = mid;
       else hi = mid;
     }
     s = lo;
   }
   for (int k = lane; k < m; k += 32) theta[k * B + b] = d[k];
-  for (int r = lane; r < m; r += 32)
-    for (int c = 0; c < m; ++c) Qout[((size_t)b * m + r) * m + c] = Q[r * m + c];
+  if constexpr (FULL)
+    for (int r = lane; r < m; r += 32)
+      for (int c = 0; c < m; ++c) Qout[((size_t)b * m + r) * m + c] = Q[r * m + c];
   if (lane == 0) sb[b] = s;
 }
 
+template <bool FULL>
 __global__ void k_tridiag_eig(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
                               const double* __restrict__ beta_last_arr, double zr, double zi, double s_target,
                               double tol, double* __restrict__ theta, double* __restrict__ Qout,
                               double* __restrict__ sb, int* status) {
-  tridiag_eig_block(m, B, alpha, beta, beta_last_arr, zr, zi, s_target, tol, theta, Qout, sb, status);
+  tridiag_eig_block<FULL>(m, B, alpha, beta, beta_last_arr, zr, zi, s_target, tol, theta, Qout, sb, status);
+}
+
+inline size_t tridiag_smem(int m, bool full) {
+  return sizeof(double) * (full ? size_t(m) * m + 2 * m + 2 : 4 * size_t(m));
 }
 
 __global__ void k_step_min(int B, const double* __restrict__ sb, double* __restrict__ sacc) {
@@ -496,12 +588,19 @@ __global__ void k_reset_ifs(IfHandles hs) {
   for (int k = 0; k < hs.n; ++k) cudaGraphSetConditional(hs.h[k], 0u);
 }
 
+// A convergence check (rows 0 and m-1 only) of the evolution graph.
 __global__ void k_tridiag_eig_dev(int m, int B, const double* __restrict__ alpha, const double* __restrict__ beta,
                                   const double* __restrict__ beta_last_arr, const ExpJob* __restrict__ job,
                                   const DevCtl* __restrict__ ctl, double* __restrict__ theta,
                                   double* __restrict__ Qout, double* __restrict__ sb, int* status) {
-  tridiag_eig_block(m, B, alpha, beta, beta_last_arr, job->zr, job->zi, ctl->s_rem, job->tol, theta, Qout, sb,
-                    status);
+  tridiag_eig_block<false>(m, B, alpha, beta, beta_last_arr, job->zr, job->zi, ctl->s_rem, job->tol, theta, Qout, sb,
+                           status);
+}
+// The full eigendecomposition of the accepted basis (dimension m_eff) for its coefficients.
+__global__ void k_tridiag_eig_full_dev(int B, const double* __restrict__ alpha, const double* __restrict__ beta,
+                                       const DevCtl* __restrict__ ctl, double* __restrict__ theta,
+                                       double* __restrict__ Qout, double* __restrict__ sb, int* status) {
+  tridiag_eig_block<true>(ctl->m_eff, B, alpha, beta, nullptr, 0.0, 0.0, 1.0, 1.0, theta, Qout, sb, status);
 }
 
 // After the check that ends Lanczos segment [.., j1): converged when the accepted step covers
@@ -935,9 +1034,9 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
       const bool last = (j1 == m);
       {
         const int mm = j1;
-        const size_t smem = sizeof(double) * (size_t(mm) * mm + 2 * mm + 2);
-        k_tridiag_eig<<<int(B), 32, smem, st>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem,
-                                                tol, ws.theta, ws.Q, ws.sb, ws.status);
+        k_tridiag_eig<false><<<int(B), 32, tridiag_smem(mm, false), st>>>(
+            mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j) * B, zr, zi, s_rem, tol, ws.theta, ws.Q, ws.sb,
+            ws.status);
         k_step_min<<<1, 32, 0, st>>>(int(B), ws.sb, ws.sacc);
         count_launch(2);
         SYK_CUDA_CHECK(cudaMemcpyAsync(hstat, ws.status, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
@@ -969,6 +1068,10 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
       set_error("expmv: Krylov step collapsed (s=%g of remaining %g); raise krylov_dim or tol", s_acc, s_rem);
       return SYK_ENUMERIC;
     }
+    // the checks kept only two rows of the eigenvectors: the full set for the coefficients
+    k_tridiag_eig<true><<<int(B), 32, tridiag_smem(m_eff, true), st>>>(
+        m_eff, int(B), ws.alpha, ws.beta, nullptr, zr, zi, 1.0, 1.0, ws.theta, ws.Q, ws.sb, ws.status);
+    count_launch();
     const bool final_basis = s_acc >= s_rem;
     // outputs whose fraction this basis reaches
     while (next < nf && (fr[next] <= s_done + s_acc * (1.0 + 1e-13) || (final_basis && next == nf - 1))) {
@@ -1167,8 +1270,8 @@ int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, boo
     capture_counts_end(&l0, &a0, kinds);
     capture_counts_begin();  // keep counting captured launches away from the global counters
     const int mm = j1;
-    const size_t smem = sizeof(double) * (size_t(mm) * mm + 2 * mm + 2);
-    k_tridiag_eig_dev<<<int(B), 32, smem, cs>>>(mm, int(B), ws.alpha, ws.beta, ws.beta + size_t(j1 - 1) * B, ws.job,
+    k_tridiag_eig_dev<<<int(B), 32, tridiag_smem(mm, false), cs>>>(mm, int(B), ws.alpha, ws.beta,
+                                                                  ws.beta + size_t(j1 - 1) * B, ws.job,
                                                 ws.ctl, ws.theta, ws.Q, ws.sb, ws.status);
     k_step_min<<<1, 32, 0, cs>>>(int(B), ws.sb, ws.sacc);
     const bool has_next = k + 1 < nseg;
@@ -1219,11 +1322,13 @@ int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, boo
   // body tail: the accepted step's coefficients, w = V c, advance
   DEV_CK(cudaStreamBeginCaptureToGraph(cs, body, fr.data(), nullptr, fr.size(), mode), "capture tail");
   k_finalize<<<1, 1, 0, cs>>>(ws.ctl, ws.sacc);
+  k_tridiag_eig_full_dev<<<int(B), 32, tridiag_smem(m, true), cs>>>(int(B), ws.alpha, ws.beta, ws.ctl, ws.theta,
+                                                                     ws.Q, ws.sb, ws.status);
   k_tridiag_coef_dev<<<int(B), 64, 0, cs>>>(int(B), ws.theta, ws.Q, ws.beta0, ws.job, ws.ctl, ws.c);
   k_combine_dev<R><<<ws.G, ws.bdim, 0, cs>>>(ws.ctl, (const typename CT<R>::T*)ws.V, size_t(ws.D * B), ws.c, ws.sc,
                                              (typename CT<R>::T*)ws.w, ws.D * B, int(B));
-  // per basis: reset, the 4 kernels of v_0, finalize, coefficients, combine, advance
-  k_advance<<<1, 1, 0, cs>>>(ws.ctl, hloop, 9);
+  // per basis: reset, the 4 kernels of v_0, finalize, eigenvectors, coefficients, combine, advance
+  k_advance<<<1, 1, 0, cs>>>(ws.ctl, hloop, 10);
   {
     cudaGraph_t tmp = body;
     DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture tail");
@@ -1442,8 +1547,8 @@ extern "C" int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const
   cudaMemsetAsync(bpad, 0, nb, st);
   cudaMemsetAsync(status, 0, 16, st);
   if (m > 1) cudaMemcpyAsync(bpad, beta, sizeof(double) * (m - 1) * B, cudaMemcpyDeviceToDevice, st);
-  const size_t smem = sizeof(double) * (size_t(m) * m + 2 * m + 2);
-  k_tridiag_eig<<<B, 32, smem, st>>>(m, B, alpha, bpad, nullptr, z_re, z_im, 1.0, 1.0, theta, Q, sb, status);
+  k_tridiag_eig<true><<<B, 32, tridiag_smem(m, true), st>>>(m, B, alpha, bpad, nullptr, z_re, z_im, 1.0, 1.0, theta, Q,
+                                                             sb, status);
   k_tridiag_coef<<<B, 64, 0, st>>>(m, B, theta, Q, beta0, z_re, z_im, nullptr, 1.0, (double2*)out);
   count_launch(2);
   cudaError_t e = cudaGetLastError();
