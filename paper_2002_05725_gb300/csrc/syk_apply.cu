@@ -684,6 +684,7 @@ int launch_apply_chi(int N, int i, int parity_in, int dtype, const void* psi, vo
 
 extern "C" int syk_apply_H(const syk_terms* terms, int parity, int dtype, const void* psi, void* y,
                            int64_t batch, void* stream) {
+  syk::NvtxRange nvtx_range_("syk_apply_H");
   syk::clear_error();
   if (!psi || !y || batch < 1) {
     syk::set_error("syk_apply_H: NULL vector or batch < 1");
@@ -746,6 +747,7 @@ extern "C" int syk_apply_chi(int N, int i, int parity_in, int dtype, const void*
 // with CUDA events on `stream` and records the fastest for later launches.
 extern "C" int syk_autotune_apply(const syk_terms* terms, int parity, int dtype, int64_t batch, int reps,
                                   void* stream, double* best_ms) {
+  syk::NvtxRange nvtx_range_("syk_autotune_apply");
   using namespace syk;
   clear_error();
   if (batch != 1 && batch != 2 && batch != 4 && batch != 8 && batch != 16) {

@@ -52,6 +52,7 @@ using namespace syk;
 extern "C" int syk_correlator_G(const syk_terms* terms, double beta, int i, const double* t, int nt, const void* psi0,
                                 int64_t nstates, int dtype, int krylov_dim, double tol, double* G_re_im, double* Z,
                                 void* stream) {
+  syk::NvtxRange nvtx_range_("syk_correlator_G");
   clear_error();
   SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, G_re_im));
   if (i < 0 || i >= terms->N) {
@@ -173,6 +174,7 @@ int otoc_impl(const syk_terms* terms, double beta, const double* x, int i, int j
 
 extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const double* t, int nt, const void* psi0,
                         int64_t nstates, int dtype, int krylov_dim, double tol, double* F_re_im, void* stream) {
+  syk::NvtxRange nvtx_range_("syk_otoc");
   clear_error();
   SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im));
   if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
@@ -187,6 +189,7 @@ extern "C" int syk_otoc(const syk_terms* terms, double beta, int i, int j, const
 extern "C" int syk_otoc_split(const syk_terms* terms, double beta, const double* x, int i, int j, const double* t,
                               int nt, const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
                               double* F_re_im, void* stream) {
+  syk::NvtxRange nvtx_range_("syk_otoc_split");
   clear_error();
   SYK_TRY(check_common(terms, beta, t, nt, psi0, nstates, dtype, krylov_dim, tol, F_re_im));
   if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
@@ -216,6 +219,7 @@ extern "C" int syk_otoc_split(const syk_terms* terms, double beta, const double*
 extern "C" int syk_correlator_G_imag(const syk_terms* terms, double beta, int i, const double* tau, int ntau,
                                      const void* psi0, int64_t nstates, int dtype, int krylov_dim, double tol,
                                      double* G_re_im, double* Z, void* stream) {
+  syk::NvtxRange nvtx_range_("syk_correlator_G_imag");
   clear_error();
   SYK_TRY(check_common(terms, beta, tau, ntau, psi0, nstates, dtype, krylov_dim, tol, G_re_im));
   if (i < 0 || i >= terms->N) {
@@ -282,6 +286,7 @@ extern "C" int syk_correlator_G_imag(const syk_terms* terms, double beta, int i,
 // distinct (N, dtype, batch) is autotuned first on the calling thread.
 extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const double* t, int nt,
                               int dtype, int krylov_dim, double tol, int nworkers, int* item_status) {
+  syk::NvtxRange nvtx_range_("syk_otoc_batch");
   clear_error();
   if (!items || nitems < 1 || nworkers < 1) {
     set_error("syk_otoc_batch: need items, nitems >= 1 and nworkers >= 1");
@@ -333,6 +338,7 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
     for (int q = next++; q < nitems; q = next++) {
       const int k = order[q];
       const syk_otoc_item& it = items[k];
+      NvtxRange item_range("syk_otoc_batch item");
       static const double quarter[4] = {0.25, 0.25, 0.25, 0.25};
       const int rc = otoc_impl(it.terms, it.beta, quarter, i, j, t, nt, it.psi0, it.nstates, dtype, krylov_dim,
                                tol, it.F_re_im, st);

@@ -72,6 +72,7 @@ using namespace syk;
 extern "C" int syk_lowest_eigenvalues(const syk_terms* terms, int parity, int dtype, const void* psi0, int k,
                                       int max_steps, double tol, double* evals, double* resid, int* nsteps,
                                       void* stream) {
+  syk::NvtxRange nvtx_range_("syk_lowest_eigenvalues");
   clear_error();
   if (!terms || !psi0 || !evals || k < 1 || !(tol > 0.0) || !dtype_ok(dtype) || (parity != 0 && parity != 1)) {
     set_error("syk_lowest_eigenvalues: invalid argument (k=%d tol=%g dtype=%d parity=%d)", k, tol, dtype, parity);

@@ -491,6 +491,7 @@ using namespace syk;
 extern "C" int syk_otoc_grad(const syk_terms* terms, double beta, int i, int j, double t, const void* psi0,
                              int64_t nstates, int dtype, int krylov_dim, double tol, double quad_dz,
                              double* Ft_re_im, double* dFt_dJ, double* dFt_dbeta, void* stream) {
+  syk::NvtxRange nvtx_range_("syk_otoc_grad");
   clear_error();
   SYK_TRY(grad_common_checks(terms, beta, t, psi0, nstates, dtype, krylov_dim, tol, quad_dz));
   if (i < 0 || i >= terms->N || j < 0 || j >= terms->N || i == j) {
@@ -558,6 +559,7 @@ extern "C" int syk_otoc_grad(const syk_terms* terms, double beta, int i, int j, 
 extern "C" int syk_correlator_G_grad(const syk_terms* terms, double beta, int i, double t, const void* psi0,
                                      int64_t nstates, int dtype, int krylov_dim, double tol, double quad_dz,
                                      double* G_re_im, double* dG_dJ, double* dG_dbeta, void* stream) {
+  syk::NvtxRange nvtx_range_("syk_correlator_G_grad");
   clear_error();
   SYK_TRY(grad_common_checks(terms, beta, t, psi0, nstates, dtype, krylov_dim, tol, quad_dz));
   if (i < 0 || i >= terms->N) {

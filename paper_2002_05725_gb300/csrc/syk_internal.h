@@ -9,9 +9,20 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/syk.h"
 
 namespace syk {
+
+// Names a span of host-side library work for profilers (NVTX ranges: a call into a stub that
+// does nothing unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void set_error(const char* fmt, ...);
 void clear_error();

@@ -1007,6 +1007,7 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
   int steps = 0, next = 0;
   const void* cur = psi;
   while (s_rem > 0.0) {
+    NvtxRange basis_range("krylov basis");
     if (++steps > 100000) {
       set_error("expmv: more than 100000 Krylov steps");
       return SYK_ENUMERIC;
@@ -1494,6 +1495,7 @@ extern "C" size_t syk_workspace_bytes(int N, int dtype, int krylov_dim, int64_t 
 extern "C" int syk_expmv(const syk_terms* terms, int parity, int dtype, double z_re, double z_im, const void* psi,
                          void* out, int64_t batch, int krylov_dim, double tol, void* workspace, size_t ws_bytes,
                          void* stream, int* nsteps) {
+  syk::NvtxRange nvtx_range_("syk_expmv");
   clear_error();
   if (!psi || !out || batch < 1 || batch > 256 || krylov_dim < 2 || krylov_dim > SYK_MAX_KRYLOV) {
     set_error("syk_expmv: invalid argument (batch=%lld krylov_dim=%d)", (long long)batch, krylov_dim);
@@ -1527,6 +1529,7 @@ extern "C" int syk_expmv(const syk_terms* terms, int parity, int dtype, double z
 
 extern "C" int syk_tridiag_expm(int m, int64_t batch, const double* alpha, const double* beta, const double* beta0,
                                 double z_re, double z_im, double* out, void* stream) {
+  syk::NvtxRange nvtx_range_("syk_tridiag_expm");
   clear_error();
   if (m < 1 || m > SYK_MAX_KRYLOV || batch < 1 || batch > 65535 || !alpha || !beta0 || !out || (m > 1 && !beta)) {
     set_error("syk_tridiag_expm: invalid argument (m=%d batch=%lld)", m, (long long)batch);
@@ -1581,6 +1584,7 @@ void* g_static_addr[128] = {};
 extern "C" int syk_expmv_static(const syk_terms* terms, int parity, int dtype, double z_re, double z_im,
                                 const void* psi, void* out, int64_t batch, int krylov_dim, double tol, void* stream,
                                 int* nsteps) {
+  syk::NvtxRange nvtx_range_("syk_expmv_static");
   clear_error();
   if (!terms || !psi || !out || batch < 1 || batch > 256 || krylov_dim < 2 || krylov_dim > SYK_MAX_KRYLOV ||
       !dtype_ok(dtype) || (parity != 0 && parity != 1)) {

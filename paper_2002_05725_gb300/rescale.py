@@ -188,6 +188,9 @@ def main():
     ap.add_argument("--krylov", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--out-dir", default=None,
+                    help="store each item's curves in this directory (one .npz per item) and reuse the ones "
+                         "already there, so that an interrupted run resumes")
     ap.add_argument("--spectral-window", action="store_true",
                     help="extrapolate over the sizes whose lowest 20 eigenstates (GPU Lanczos on the first "
                          "coupling draw) lie within 1/beta of the ground state")
@@ -195,17 +198,25 @@ def main():
     syk.load()
     Ns = [int(v) for v in a.N.split(",")]
     t = np.round(np.arange(0.0, a.tmax + 0.5 * a.dt, a.dt), 12)
-    items, keys = [], []
-    for N in Ns:
-        for r in range(a.draws):
-            terms = syk.syk_build_terms(N, inputs.couplings(N, seed=0, realization=r))
-            psi = torch.from_numpy(np.ascontiguousarray(inputs.random_states(N, a.states, 0, r).T)).to(
-                torch.complex64).cuda()
-            items.append((terms, a.beta, psi))
-            keys.append(N)
-    torch.cuda.synchronize()
+    keys = [N for N in Ns for _ in range(a.draws)]
     t0 = time.perf_counter()
-    Fs = syk.syk_otoc_batch(items, 0, 1, t, syk.SYK_C64, a.krylov, a.tol, a.workers)
+    if a.out_dir:
+        from . import curves
+        specs = [{"N": N, "seed": 0, "realization": r, "beta": a.beta, "states": a.states}
+                 for N in Ns for r in range(a.draws)]
+        Fs, _ = curves.run_otoc_items(specs, t, a.out_dir, dtype=syk.SYK_C64, krylov_dim=a.krylov, tol=a.tol,
+                                      nworkers=a.workers)
+    else:
+        items = []
+        for N in Ns:
+            for r in range(a.draws):
+                terms = syk.syk_build_terms(N, inputs.couplings(N, seed=0, realization=r))
+                psi = torch.from_numpy(np.ascontiguousarray(inputs.random_states(N, a.states, 0, r).T)).to(
+                    torch.complex64).cuda()
+                items.append((terms, a.beta, psi))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Fs = syk.syk_otoc_batch(items, 0, 1, t, syk.SYK_C64, a.krylov, a.tol, a.workers)
     wall = time.perf_counter() - t0
     Ft = {N: disorder_average([F for F, k in zip(Fs, keys) if k == N]) for N in Ns}
     use, low, resid, eig_s = None, {}, {}, 0.0
@@ -232,7 +243,7 @@ def main():
                     "E20_minus_E0": {str(N): float(low[N][19] - low[N][0]) for N in Ns},
                     "eig_max_residual": {str(N): resid[N] for N in Ns}})
     res.update({"states": a.states, "draws": a.draws, "t_grid": [float(t[0]), float(t[-1]), a.dt],
-                "otoc_seconds": wall, "curves": len(items) * a.states, "dtype": "c64"})
+                "otoc_seconds": wall, "curves": len(keys) * a.states, "dtype": "c64"})
     print(json.dumps(res))
 
 
