@@ -59,6 +59,10 @@
 #ifndef SYK_SHARED_COEF
 #define SYK_SHARED_COEF 1
 #endif
+// One-state complex64 launches use k_apply_one (syk_apply_one.cu); 0 keeps k_apply_tiled<float, 1>.
+#ifndef SYK_ONE_STATE_KERNEL
+#define SYK_ONE_STATE_KERNEL 1
+#endif
 #define SYK_PRAGMA(x) _Pragma(#x)
 #define SYK_UNROLL(n) SYK_PRAGMA(unroll n)
 
@@ -532,6 +536,8 @@ int launch_tiled(const ApplyParams& p, const void* psi, void* y, cudaStream_t st
     set_error("apply_H: %lld CTAs exceed the epilogue buffer (%lld)", (long long)(ntiles * cs), (long long)p.ep_cap);
     return SYK_EINVAL;
   }
+  if constexpr (std::is_same<R, float>::value && BT == 1 && SYK_ONE_STATE_KERNEL)
+    return launch_one_state(p, groups, ng, ntb, cs, psi, y, st);
   const size_t smem = Cfg::smem(T);
   SYK_TRY(ensure_smem_limit((const void*)k_apply_tiled<R, BT, false>, (int)Cfg::smem(Cfg::RPT << 8)));
   SYK_TRY(ensure_smem_limit((const void*)k_apply_tiled<R, BT, true>, (int)Cfg::smem(Cfg::RPT << 8)));

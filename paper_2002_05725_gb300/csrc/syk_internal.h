@@ -76,6 +76,7 @@ struct ApplyParams {
   const float4* m4_tdf;    // double-float tables (complex128 matvec in FP32 arithmetic)
   const float4* m2_tdf;
   const float2* wd_df;
+  double rho;              // host-side: spectral half-width estimate of H (term set's rho_est)
   const syk_terms* terms;  // host-side: tile-group lists
   bool no_alloc;           // host-side: never allocate (use only cached tile-group lists)
   void* df_split;          // host-side: device buffer (>= D x batch x 16 bytes) for the split
@@ -135,6 +136,12 @@ bool coset_fits(int64_t batch, int var, int ntb);  // CTA width 2^ntb (6 or 7) w
 int launch_coset_var(const ApplyParams& p, int64_t batch, const void* psi, void* y, cudaStream_t st, int var, int ntb,
                      int cs);
 
+// complex64 matvec of one state (syk_apply_one.cu) on the tiles of k_apply_tiled<float, 1>
+// (8 rows per thread, CTA width 2^ntb, ntb in 6..8, cluster of cs CTAs; groups: the chunk list
+// of that tile size).
+int launch_one_state(const ApplyParams& p, const int4* groups, int ng, int ntb, int cs, const void* psi, void* y,
+                     cudaStream_t st);
+
 int ensure_device_tables(const syk_terms* t);
 int ensure_grad_groups(const syk_terms* t);  // builds and uploads the gradient term groups
 int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p);
@@ -189,6 +196,7 @@ struct syk_terms {
   std::vector<uint64_t> xm, zm;  // per term, lexicographic order
   std::vector<uint8_t> ph;
   std::vector<double> J;
+  double rho_est = 0.0;  // 2 sqrt(sum J^2 / 16): half-width of the spectrum (RMS level x 2)
   int n4 = 0, n2 = 0;
   std::vector<uint32_t> m4_rec;  // 4 words per mask
   std::vector<double> m4_tab;    // n4 * 32 * 2

@@ -584,6 +584,11 @@ __global__ void k_job_begin(const ExpJob* job, DevCtl* ctl, cudaGraphConditional
   cudaGraphSetConditional(h_loop, (job->zr != 0.0 || job->zi != 0.0) ? 1u : 0u);
 }
 
+// Start of a basis: the first basis of the evolution (no bases yet) or a restart.
+__global__ void k_basis_head(const DevCtl* ctl, cudaGraphConditionalHandle h_first) {
+  cudaGraphSetConditional(h_first, ctl->jsteps == 0 ? 1u : 0u);
+}
+
 __global__ void k_reset_ifs(IfHandles hs) {
   for (int k = 0; k < hs.n; ++k) cudaGraphSetConditional(hs.h[k], 0u);
 }
@@ -972,16 +977,45 @@ int run_segment_graphed(const ApplyParams& P, const KrylovWS& ws, int dtype, int
   return SYK_OK;
 }
 
-// Convergence of a sub-step is checked after 4 vectors and then every `every` vectors.  A
-// check (eigensolve of T, ~0.4 ms) against the matvecs it can save: with c = check / matvec
-// cost, checking every k vectors of a basis that converges after ~m/2 vectors costs m/(2k)
-// checks plus ~k/2 matvecs of overshoot, least at k = sqrt(m c / 2).  The matvec cost is
+// When to check a Krylov basis for convergence (one plan per evolution, the same for the host-
+// and the device-driven paths).  The Lanczos approximation of e^{tau H} for a spectrum of
+// half-width rho needs about the smallest k with (e rho |tau| / 2k)^k <= tol vectors; with
+// rho = 2 x the RMS level this predicts the counts measured at N = 40 (808 matvecs per OTOC
+// curve) but overestimates by a few vectors (more at tight tol: measured, checking 2 vectors
+// before the prediction added 3 % matvecs at tol 1e-7 and 12 % at 1e-12), so the first check
+// comes at 3/4 of it (at least after 4 vectors, at most at m), the next ones every `every`
+// vectors: 2 when a matvec costs more than a check (~0.2 ms), else 4.  The matvec cost is
 // modelled from its work (8 nnz B flop at ~20 TFLOP/s for complex64, ~4.4 for complex128,
-// plus 10 us); large states come out at every 2 vectors, N = 32 with 8 states at 6, N <= 28 at 16.
-int check_every(const ApplyParams& P, int dtype, int64_t D, int64_t B, int m) {
+// plus 10 us).
+struct CheckPlan {
+  int first, every;
+};
+CheckPlan check_plan(const ApplyParams& P, int dtype, int64_t D, int64_t B, int m, std::complex<double> z,
+                     double tol) {
   const double nnz = double(D) * double(P.n4 + P.n2 + 1);
   const double apply_ms = 0.01 + 8.0 * nnz * double(B) / (dtype == SYK_C64 ? 2.0e10 : 4.4e9);
-  return std::max(2, std::min(16, int(std::lround(std::sqrt(0.5 * double(m) * 0.4 / apply_ms)))));
+  const int every = apply_ms >= 0.2 ? 2 : 4;
+  const double rt = std::abs(z) * P.rho;
+  int k = m + 1;
+  for (int kk = 1; kk <= m; ++kk)
+    if (rt <= 0.0 || double(kk) * std::log(2.718281828459045 * rt / (2.0 * kk)) <= std::log(tol)) {
+      k = kk;
+      break;
+    }
+  const int first = std::min(m, std::max(4, (3 * k) / 4));
+  return {first, every};
+}
+
+// Segment ends of a basis under a plan: the first check, then every `every` vectors, and m.
+std::vector<int> segment_ends(int m, const CheckPlan& pl) {
+  std::vector<int> e;
+  int j1 = std::min(m, std::max(1, pl.first));
+  e.push_back(j1);
+  while (j1 < m) {
+    j1 = std::min(m, j1 + pl.every);
+    e.push_back(j1);
+  }
+  return e;
 }
 
 // outs[k] = e^{fr[k] z H} psi for 0 < fr[0] < ... < fr[nf-1]: the step to fr[nf-1] is split
@@ -998,7 +1032,9 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
   // reaches; complex128 vectors get the second pass ("twice is enough")
   const bool two_pass = dtype == SYK_C128;
   const int orth = lanczos_orth(dtype);
-  const int every = check_every(P, dtype, ws.D, B, m);
+  const CheckPlan plan = check_plan(P, dtype, ws.D, B, m, z, tol);
+  // the first basis checks by the plan; a restart covers an unknown remainder: from 4 vectors on
+  const std::vector<int> ends_first = segment_ends(m, plan), ends_restart = segment_ends(m, CheckPlan{4, plan.every});
   const double zr = z.real(), zi = z.imag();
   int* hstat = static_cast<int*>(ws.host_stage ? ws.host_stage : pinned_scratch(64));
   double* hs = reinterpret_cast<double*>(hstat + 4);
@@ -1025,10 +1061,10 @@ int expmv_T(const ApplyParams& P_in, int dtype, std::complex<double> z, const vo
       for (int j = j0; j < j1; ++j) SYK_TRY(lanczos_step<R>(P, dtype, ws, j, orth, two_pass, bt, st));
       return SYK_OK;
     };
+    const std::vector<int>& ends = steps == 1 ? ends_first : ends_restart;
     int j0 = 0;
-    while (j0 < m) {
-      int j1 = j0 + 1;
-      while (!(j1 == m || j1 == 4 || (j1 > 4 && j1 % every == 0))) ++j1;
+    for (size_t si = 0; si < ends.size() && j0 < m; ++si) {
+      const int j1 = ends[si];
       SYK_TRY(run_segment_graphed(P, ws, dtype, B, m, j0, j1, two_pass, st,
                                   [&](cudaStream_t s) { return segment(j0, j1, s); }));
       const int j = j1 - 1;
@@ -1159,11 +1195,11 @@ struct DevKey {
   const void* tab;
   int sector, dtype;
   int64_t B, D;
-  int m, orth, every;
+  int m, orth, first, every;
   uint64_t epoch;
   bool operator<(const DevKey& o) const {
-    return std::tie(V, tab, sector, dtype, B, D, m, orth, every, epoch) <
-           std::tie(o.V, o.tab, o.sector, o.dtype, o.B, o.D, o.m, o.orth, o.every, o.epoch);
+    return std::tie(V, tab, sector, dtype, B, D, m, orth, first, every, epoch) <
+           std::tie(o.V, o.tab, o.sector, o.dtype, o.B, o.D, o.m, o.orth, o.first, o.every, o.epoch);
   }
 };
 struct DevCache {
@@ -1192,8 +1228,8 @@ std::vector<cudaGraphNode_t> capture_frontier(cudaStream_t s) {
 //   copy w -> out.
 // The segments and checks are exactly expmv_T's, so results equal the host-driven path's.
 template <typename R>
-int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, bool two_pass, int every, double bt,
-                    cudaStream_t st, cudaGraphExec_t* out) {
+int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, bool two_pass, const CheckPlan& plan,
+                    double bt, cudaStream_t st, cudaGraphExec_t* out) {
   const int64_t B = ws.B;
   const int m = ws.m;
   if (!t_dev.cap) SYK_CUDA_CHECK(cudaStreamCreateWithFlags(&t_dev.cap, cudaStreamNonBlocking));
@@ -1206,17 +1242,11 @@ int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, boo
   const int wrc = launch_apply_H(P, dtype, ws.vec(0), ws.w, B, st);
   capture_counts_end(&wl, &wa, wk);
   SYK_TRY(wrc);
-  // segment ends: after 4 vectors, then at multiples of `every`, and at m (as in expmv_T)
-  std::vector<int> j1s;
-  for (int j0 = 0; j0 < m;) {
-    int j1 = j0 + 1;
-    while (!(j1 == m || j1 == 4 || (j1 > 4 && j1 % every == 0))) ++j1;
-    j1s.push_back(j1);
-    j0 = j1;
-  }
-  const int nseg = int(j1s.size());
-  if (nseg > kMaxSegs) {
-    set_error("expmv graph: %d segments exceed %d", nseg, kMaxSegs);
+  // segment ends: the evolution's check plan for its first basis, checks from 4 vectors on
+  // for restarts (as in expmv_T)
+  const std::vector<int> j1s_first = segment_ends(m, plan), j1s_restart = segment_ends(m, CheckPlan{4, plan.every});
+  if (int(j1s_restart.size()) > kMaxSegs) {
+    set_error("expmv graph: %d segments exceed %d", int(j1s_restart.size()), kMaxSegs);
     return SYK_EINVAL;
   }
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
@@ -1260,11 +1290,11 @@ int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, boo
   cudaGraphNode_t wnode;
   DEV_CK(cudaGraphAddNode(&wnode, g, fr.data(), nullptr, fr.size(), &wp), "while node");
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  IfHandles ifs = {};
-  ifs.n = nseg - 1;
-  for (int k = 0; k < ifs.n; ++k) DEV_CK(cudaGraphConditionalHandleCreate(&ifs.h[k], body, 0, 0), "if handle");
-  // one segment of Lanczos steps [j0, j1) and its convergence check, captured on cs
-  auto segment = [&](int k, int j0, int j1) -> int {
+  cudaGraphConditionalHandle hfirst;
+  DEV_CK(cudaGraphConditionalHandleCreate(&hfirst, body, 0, 0), "first-basis handle");
+  // one segment of Lanczos steps [j0, j1) and its convergence check, captured on cs; its
+  // decide kernel opens the next segment of the chain (handle ifs.h[k])
+  auto segment = [&](const IfHandles& ifs, int k, int j0, int j1) -> int {
     int64_t l0 = 0, a0 = 0, kinds[kMvKinds];
     capture_counts_begin();  // the segment's own tallies (launches and matvecs per execution)
     for (int j = j0; j < j1; ++j) SYK_TRY(lanczos_step<R>(P, dtype, ws, j, orth, two_pass, bt, cs));
@@ -1273,53 +1303,82 @@ int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, boo
     const int mm = j1;
     k_tridiag_eig_dev<<<int(B), 32, tridiag_smem(mm, false), cs>>>(mm, int(B), ws.alpha, ws.beta,
                                                                   ws.beta + size_t(j1 - 1) * B, ws.job,
-                                                ws.ctl, ws.theta, ws.Q, ws.sb, ws.status);
+                                                                  ws.ctl, ws.theta, ws.Q, ws.sb, ws.status);
     k_step_min<<<1, 32, 0, cs>>>(int(B), ws.sb, ws.sacc);
-    const bool has_next = k + 1 < nseg;
+    const bool has_next = k < ifs.n;
     k_decide<<<1, 1, 0, cs>>>(ws.ctl, j1, j1 == m ? 1 : 0, ws.status, P.status, ws.sacc,
                               has_next ? ifs.h[k] : cudaGraphConditionalHandle(0), has_next ? 1 : 0, a0, l0 + 3,
                               kinds[kMvRows], kinds[kMvTiled], kinds[kMvCoset]);
     SYK_CUDA_CHECK(cudaGetLastError());
     return SYK_OK;
   };
-  // body head: reset the IF handles, v_0 = w / |w|, first segment
+  // the segments ending at `ends`, captured into graph gb: reset the chain's IF handles, the
+  // first segment, then one IF node per later segment
+  auto build_chain = [&](cudaGraph_t gb, const std::vector<int>& ends) -> int {
+    IfHandles ifs = {};
+    ifs.n = int(ends.size()) - 1;
+    for (int k = 0; k < ifs.n; ++k) SYK_CUDA_CHECK(cudaGraphConditionalHandleCreate(&ifs.h[k], gb, 0, 0));
+    SYK_CUDA_CHECK(cudaStreamBeginCaptureToGraph(cs, gb, nullptr, nullptr, 0, mode));
+    k_reset_ifs<<<1, 1, 0, cs>>>(ifs);
+    int crc = segment(ifs, 0, 0, ends[0]);
+    std::vector<cudaGraphNode_t> cf = capture_frontier(cs);
+    {
+      cudaGraph_t tmp = gb;
+      const cudaError_t e = cudaStreamEndCapture(cs, &tmp);
+      if (crc == SYK_OK && e != cudaSuccess) {
+        set_error("expmv graph: end capture: %s", cudaGetErrorString(e));
+        crc = SYK_ECUDA;
+      }
+    }
+    if (crc != SYK_OK) return crc;
+    for (int k = 1; k < int(ends.size()); ++k) {
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = ifs.h[k - 1];
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t inode;
+      SYK_CUDA_CHECK(cudaGraphAddNode(&inode, gb, cf.data(), nullptr, cf.size(), &ip));
+      cudaGraph_t ib = ip.conditional.phGraph_out[0];
+      SYK_CUDA_CHECK(cudaStreamBeginCaptureToGraph(cs, ib, nullptr, nullptr, 0, mode));
+      crc = segment(ifs, k, ends[k - 1], ends[k]);
+      cudaGraph_t tmp = ib;
+      const cudaError_t e = cudaStreamEndCapture(cs, &tmp);
+      if (crc != SYK_OK) return crc;
+      SYK_CUDA_CHECK(e);
+      cf = {inode};
+    }
+    return SYK_OK;
+  };
+  // body head: first basis of the evolution or a restart, v_0 = w / |w|
   DEV_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode), "capture body");
-  k_reset_ifs<<<1, 1, 0, cs>>>(ifs);
+  k_basis_head<<<1, 1, 0, cs>>>(ws.ctl, hfirst);
   Ops<R>::dots(ws, 1, ws.w, 0, ws.w, cs);
   reduce_parts(ws, 1, ws.h1, cs);
   k_norm_init<<<(int(B) + 127) / 128, 128, 0, cs>>>(int(B), ws.h1, ws.beta0, ws.inv, ws.sc, ws.status);
   Ops<R>::scale(ws, ws.w, ws.vec(0), ws.inv, cs);
-  rc = segment(0, 0, j1s[0]);
   fr = capture_frontier(cs);
   {
     cudaGraph_t tmp = body;
     DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture body");
   }
+  // the first basis checks by the evolution's plan, restarts from 4 vectors on
+  cudaGraphNodeParams bp = {};
+  bp.type = cudaGraphNodeTypeConditional;
+  bp.conditional.handle = hfirst;
+  bp.conditional.type = cudaGraphCondTypeIf;
+  bp.conditional.size = 2;
+  cudaGraphNode_t bnode;
+  DEV_CK(cudaGraphAddNode(&bnode, body, fr.data(), nullptr, fr.size(), &bp), "first/restart node");
+  cudaGraph_t first_branch = bp.conditional.phGraph_out[0], restart_branch = bp.conditional.phGraph_out[1];
+  rc = build_chain(first_branch, j1s_first);
+  if (rc == SYK_OK) rc = build_chain(restart_branch, j1s_restart);
   if (rc != SYK_OK) {
+    cudaGetLastError();
     cudaGraphDestroy(g);
     return rc;
   }
-  for (int k = 1; k < nseg; ++k) {
-    cudaGraphNodeParams ip = {};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = ifs.h[k - 1];
-    ip.conditional.type = cudaGraphCondTypeIf;
-    ip.conditional.size = 1;
-    cudaGraphNode_t inode;
-    DEV_CK(cudaGraphAddNode(&inode, body, fr.data(), nullptr, fr.size(), &ip), "if node");
-    cudaGraph_t ib = ip.conditional.phGraph_out[0];
-    DEV_CK(cudaStreamBeginCaptureToGraph(cs, ib, nullptr, nullptr, 0, mode), "capture if");
-    rc = segment(k, j1s[k - 1], j1s[k]);
-    {
-      cudaGraph_t tmp = ib;
-      DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture if");
-    }
-    if (rc != SYK_OK) {
-      cudaGraphDestroy(g);
-      return rc;
-    }
-    fr = {inode};
-  }
+  fr = {bnode};
   // body tail: the accepted step's coefficients, w = V c, advance
   DEV_CK(cudaStreamBeginCaptureToGraph(cs, body, fr.data(), nullptr, fr.size(), mode), "capture tail");
   k_finalize<<<1, 1, 0, cs>>>(ws.ctl, ws.sacc);
@@ -1328,8 +1387,8 @@ int build_dev_graph(const ApplyParams& P, int dtype, KrylovWS& ws, int orth, boo
   k_tridiag_coef_dev<<<int(B), 64, 0, cs>>>(int(B), ws.theta, ws.Q, ws.beta0, ws.job, ws.ctl, ws.c);
   k_combine_dev<R><<<ws.G, ws.bdim, 0, cs>>>(ws.ctl, (const typename CT<R>::T*)ws.V, size_t(ws.D * B), ws.c, ws.sc,
                                              (typename CT<R>::T*)ws.w, ws.D * B, int(B));
-  // per basis: reset, the 4 kernels of v_0, finalize, eigenvectors, coefficients, combine, advance
-  k_advance<<<1, 1, 0, cs>>>(ws.ctl, hloop, 10);
+  // per basis: head, the 4 kernels of v_0, reset, finalize, eigenvectors, coefficients, combine, advance
+  k_advance<<<1, 1, 0, cs>>>(ws.ctl, hloop, 11);
   {
     cudaGraph_t tmp = body;
     DEV_CK(cudaStreamEndCapture(cs, &tmp), "end capture tail");
@@ -1373,8 +1432,8 @@ int expmv_chain(const ApplyParams& P_in, int dtype, std::complex<double> z, cons
   }
   const ApplyParams P = ws.with_split(P_in);
   const int orth = lanczos_orth(dtype);
-  const int every = check_every(P, dtype, ws.D, B, ws.m);
-  const DevKey key{ws.V, P.m4_tab, P.sector, dtype, B, P.D, ws.m, orth, every, graph_epoch()};
+  const CheckPlan plan = check_plan(P, dtype, ws.D, B, ws.m, z, tol);
+  const DevKey key{ws.V, P.m4_tab, P.sector, dtype, B, P.D, ws.m, orth, plan.first, plan.every, graph_epoch()};
   auto it = t_dev.graphs.find(key);
   if (it == t_dev.graphs.end()) {
     if (t_dev.graphs.size() > 256) {
@@ -1383,8 +1442,8 @@ int expmv_chain(const ApplyParams& P_in, int dtype, std::complex<double> z, cons
     }
     const double bt = (dtype == SYK_C64 ? 64.0 * 5.96e-8 : 64.0 * 1.11e-16);
     cudaGraphExec_t exec = nullptr;
-    const int rc = dtype == SYK_C64 ? build_dev_graph<float>(P, dtype, ws, orth, false, every, bt, st, &exec)
-                                    : build_dev_graph<double>(P, dtype, ws, orth, true, every, bt, st, &exec);
+    const int rc = dtype == SYK_C64 ? build_dev_graph<float>(P, dtype, ws, orth, false, plan, bt, st, &exec)
+                                    : build_dev_graph<double>(P, dtype, ws, orth, true, plan, bt, st, &exec);
     if (rc != SYK_OK) return rc;
     it = t_dev.graphs.emplace(key, exec).first;
   }

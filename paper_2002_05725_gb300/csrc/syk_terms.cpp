@@ -253,8 +253,13 @@ extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
     }
     t->n4 = int(r4.size());
     t->n2 = int(r2.size());
-    for (double v : t->J)
+    double sum2 = 0.0;
+    for (double v : t->J) {
       if (!std::isfinite(v)) throw std::runtime_error("non-finite coupling");
+      sum2 += v * v;
+    }
+    // Tr H^2 / 2^n = sum J^2 / 16: the RMS eigenvalue; twice it bounds the bulk of the spectrum
+    t->rho_est = 2.0 * std::sqrt(sum2 / 16.0);
   } catch (const std::bad_alloc&) {
     delete t;
     set_error("syk_build_terms: out of host memory");
@@ -404,6 +409,7 @@ int make_apply_params(const syk_terms* t, int parity, int dtype, ApplyParams* p)
   p->m2_tab = f ? (const void*)t->dev.m2_t32 : (const void*)t->dev.m2_t64;
   p->wd = f ? (const void*)t->dev.wd32 : (const void*)t->dev.wd64;
   p->status = t->dev.status;
+  p->rho = t->rho_est;
   p->m4_tdf = t->dev.m4_tdf;
   p->m2_tdf = t->dev.m2_tdf;
   p->wd_df = t->dev.wd_df;
