@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) k_apply_tiled(ApplyParams p, const int4* 
   uint32_t soff[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) soff[k] = CH ? (uint32_t)(((k + rho) & (CH - 1)) * 16) : 0u;
-  const int fsh = 5 * (ntb - 6);  // flip patterns of row bits ntb, ntb+1, ntb+2
+  const int fsh = flip_shift(ntb);  // flip patterns of row bits ntb, ntb+1, ntb+2
   uint32_t xf[RPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {

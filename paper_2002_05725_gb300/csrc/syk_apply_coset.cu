@@ -16,6 +16,7 @@
 
 #include <cstdint>
 
+#include "syk_coset.cuh"
 #include "syk_tile.cuh"
 
 #ifndef SYK_GMAX
@@ -35,21 +36,6 @@ struct CosetCfg {
   static constexpr int AUXB = GMAX * (TABB + 16);  // tables and mask records
   static size_t buf_bytes(int T) { return (size_t)T * ROWB + AUXB; }
   static size_t smem(int T) { return 2 * buf_bytes(T) + 64; }
-};
-
-template <int RB>
-struct CosetShapes;  // the member sets the host builder lists, in its order
-template <>
-struct CosetShapes<1> {
-  static constexpr uint32_t n = 1, s0 = 0x3u, s1 = 0u, s2 = 0u;
-};
-template <>
-struct CosetShapes<2> {
-  static constexpr uint32_t n = 2, s0 = 0x7u, s1 = 0xEu, s2 = 0u;
-};
-template <>
-struct CosetShapes<3> {
-  static constexpr uint32_t n = 3, s0 = 0x17u, s1 = 0xE8u, s2 = 0x7Eu;
 };
 
 // One coset of member set SH whose records start at srec[mb]: members j = 0.. in offset order.
@@ -128,7 +114,7 @@ __global__ void __launch_bounds__(1 << NTB) k_apply_coset(ApplyParams p, const i
   uint32_t soff[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) soff[k] = (uint32_t)(((k + rho) & (CH - 1)) * 16);
-  constexpr int fsh = 5 * (NTB - 6);
+  constexpr int fsh = flip_shift(NTB);
   uint32_t xf[RPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(1 << NTB) k_apply_one(ApplyParams p, const int
                                                     const float2* __restrict__ psi, float2* __restrict__ y) {
   constexpr int RPT = OneCfg::RPT, GMAX = OneCfg::GMAX, TABB = OneCfg::TABB;
   constexpr int NT = 1 << NTB, T = RPT << NTB, TILEB = T * 8, BUFB = TILEB + OneCfg::AUXB;
-  constexpr int fsh = 5 * (NTB - 6);  // flip patterns of row bits ntb, ntb+1, ntb+2
+  constexpr int fsh = flip_shift(NTB);  // flip patterns of row bits ntb, ntb+1, ntb+2
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * BUFB);
   const float2* __restrict__ t4 = static_cast<const float2*>(p.m4_tab);

@@ -42,6 +42,12 @@ void clear_error();
     if (rc_ != SYK_OK) return rc_; \
   } while (0)
 
+// Row-flip patterns of a popcount-4 mask record (.w): 5 bits (4 table-index support bits and
+// the sign bit) per compact row bit kFlipBit0 .. kFlipBit0 + 5; a kernel whose row slots are
+// the compact bits b .. b+2 reads them at shift 5 * (b - kFlipBit0).
+constexpr int kFlipBit0 = 5;
+constexpr int flip_shift(int b) { return 5 * (b - kFlipBit0); }
+
 // Device copies of the grouped coefficient tables (see syk_terms.cpp for the math).
 struct DeviceTables {
   int device = -1;

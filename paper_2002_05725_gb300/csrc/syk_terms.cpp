@@ -188,11 +188,11 @@ extern "C" int syk_build_terms(int N, const double* J, syk_terms** out) {
         // shift by pos[k] - k (pos is ascending, so every shift is >= 0)
         r.supp = uint32_t(pos[0]) | uint32_t(pos[1] - 1) << 8 | uint32_t(pos[2] - 2) << 16 |
                  uint32_t(pos[3] - 3) << 24;
-        // Table-index change when compact row bit j flips (j = 6..10): bit j of the full index
-        // flips and so does the top bit n-1 (the parity of the compact index).
+        // Table-index change when compact row bit j flips (j = syk::kFlipBit0 .. +5): bit j
+        // of the full index flips and so does the top bit n-1 (the parity of the compact index).
         const int top = n - 1;
-        for (int b = 0; b < 5; ++b) {
-          const int j = 6 + b;
+        for (int b = 0; b < 6; ++b) {
+          const int j = syk::kFlipBit0 + b;
           uint32_t f = 0;
           if (j < top) {
             for (int k = 0; k < 4; ++k)
