@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <type_traits>
 #include <vector>
 
 #include "syk_cplx.cuh"
@@ -30,87 +31,201 @@
 namespace syk {
 namespace {
 
-__device__ __forceinline__ uint32_t grad_supp_bits(uint32_t xf, uint32_t s) {
-  return (__funnelshift_r(xf, 0u, s) & 1u) | (__funnelshift_r(xf, 0u, s >> 8) & 2u) |
-         (__funnelshift_r(xf, 0u, s >> 16) & 4u) | (__funnelshift_r(xf, 0u, s >> 24) & 8u);
+// v's bits deposited, lowest first, at the set bits of mask
+__device__ __forceinline__ uint32_t deposit_bits(uint32_t v, uint32_t mask) {
+  uint32_t r = 0;
+  for (uint32_t bit = 1; mask; bit <<= 1) {
+    const uint32_t low = mask & (0u - mask);
+    if (v & bit) r |= low;
+    mask ^= low;
+  }
+  return r;
 }
 
-// partial[((g*RC + chunk)*16 + s)*B + b] = sum over the chunk's rows of
-// conj(lam[x][b]) psi[x^m][b] (-1)^popcount(zeta & xf) (-1)^popcount(s & u(xf)).
-// Each thread bins its rows' products by the support bits u in its own shared-memory slots
-// (bins[u][thread], conflict-free, one read-modify-write per row), applies the Walsh
-// transform over u to its bins once, and the threads of each column are then summed in a
-// fixed order: deterministic, and O(1) work per row instead of 2^k signed additions.
+// Blocks of 2^G rows xb + o_q of one thread (term kernel below): the G lowest walked bits in
+// Gray order (o_q = their deposit of q ^ (q >> 1)), the other walked bits (hmask) in
+// increasing order.  Within a block the row parity alternates (pb, pb^1, ...) and the zeta sign
+// is the block's sign times a per-thread constant f_q, so only xb needs popcounts; lam rows sit
+// at xb + o_q and psi rows at (xb ^ m) + d_q, because xb has no bits at the Gray bits.
+template <int G, typename R, typename C>
+__device__ __forceinline__ void term_blocks(const C* __restrict__ lam, const C* __restrict__ psi, size_t bs, int col,
+                                            uint32_t x0, uint32_t jmask, uint4 rec, int nb, int sector, R& a0r,
+                                            R& a0i, R& a1r, R& a1i) {
+  constexpr int NQ = 1 << G;
+  uint32_t e[G], low = 0, rest = jmask;
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    e[i] = rest & (0u - rest);
+    rest ^= e[i];
+    low |= e[i];
+  }
+  const uint32_t hmask = rest, mj = rec.x & low;
+  const uint32_t zc = rec.y & ((1u << nb) - 1u), zt = (rec.y >> nb) & 1u;
+  ptrdiff_t lo[NQ], po[NQ];
+  R f[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const uint32_t gq = (uint32_t)(q ^ (q >> 1));
+    uint32_t o = 0;
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+      if ((gq >> i) & 1u) o |= e[i];
+    lo[q] = (ptrdiff_t)o * (ptrdiff_t)bs;
+    po[q] = ((ptrdiff_t)(mj ^ o) - (ptrdiff_t)mj) * (ptrdiff_t)bs;
+    f[q] = ((__popc(zc & o) ^ (zt & (uint32_t)(q & 1))) & 1) ? R(-1) : R(1);
+  }
+  uint32_t hi = 0;
+  do {
+    const uint32_t xb = x0 | hi;
+    const C* lb = lam + (size_t)xb * bs + col;
+    const C* pb_ = psi + (size_t)(xb ^ rec.x) * bs + col;
+    C l[NQ], p[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      l[q] = lb[lo[q]];
+      p[q] = pb_[po[q]];
+    }
+    const uint32_t pb = (uint32_t)((__popc(xb) + sector) & 1);
+    const uint32_t sg = (uint32_t)(__popc(zc & xb) & 1) ^ (zt & pb);
+    // even rows (parity pb) and odd rows (parity pb ^ 1), signs applied: conj(l) p
+    R er = R(0), ei = R(0), orr = R(0), oi = R(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const R xr = f[q] * (l[q].x * p[q].x + l[q].y * p[q].y);
+      const R xi = f[q] * (l[q].x * p[q].y - l[q].y * p[q].x);
+      if (q & 1) {
+        orr += xr;
+        oi += xi;
+      } else {
+        er += xr;
+        ei += xi;
+      }
+    }
+    if (sg) {
+      er = -er;
+      ei = -ei;
+      orr = -orr;
+      oi = -oi;
+    }
+    if (pb) {
+      a1r += er;
+      a1i += ei;
+      a0r += orr;
+      a0i += oi;
+    } else {
+      a0r += er;
+      a0i += ei;
+      a1r += orr;
+      a1i += oi;
+    }
+    hi = ((hi | ~hmask) + 1u) & hmask;
+  } while (hi != 0u);
+}
+
+// partial[((g*RC + chunk)*16 + s)*Bt + c0 + b] = sum over the rows x of the chunk of
+// conj(lam[x][c0+b]) psi[x^m][c0+b] (-1)^popcount(zeta & xf) (-1)^popcount(s & u(xf)), u(xf) = the
+// bits of the full index xf at the group's k support positions.
+// The rows of the nb-bit compact index are enumerated per group: the LB lane bits of a thread
+// (r = tid / Bc) are the support positions below the top spin plus the lowest other bits, the
+// CB chunk bits the highest of the rest, and the thread walks the remaining bits.  So u is the
+// same for all rows of a thread except for the top spin (the parity bit, set by the row), and
+// the thread sums its products in two register pairs (parity 0 and 1), without a per-row
+// shared-memory update.  Then each thread forms the 2^k-point Walsh transform of its (at most
+// two) nonzero bins, and the threads of each column are summed in a fixed order
+// (deterministic).  Lanes r >= 2^LB (sectors smaller than the lane count) hold no rows.
 template <typename R>
-__global__ void k_term_grad(const uint4* __restrict__ grec, int n, int sector, int64_t D, int B,
+__global__ void k_term_grad(const uint4* __restrict__ grec, int n, int sector, int LB, int CB, int Bt, int c0, int Bc,
                             const typename CT<R>::T* __restrict__ lam, const typename CT<R>::T* __restrict__ psi,
                             double2* __restrict__ partial) {
   using C = typename CT<R>::T;
   extern __shared__ __align__(16) unsigned char tg_smem[];
-  R* bins = reinterpret_cast<R*>(tg_smem);  // [32][NT]: real parts of u = 0..15, then imaginary parts
+  R* bins = reinterpret_cast<R*>(tg_smem);  // [32][NT]: real parts of s = 0..15, then imaginary parts
   const int g = blockIdx.x, chunk = blockIdx.y, RC = gridDim.y;
   const int tid = threadIdx.x, NT = blockDim.x;
+  const int b = tid % Bc, r = tid / Bc;
+  const int rows_per_pass = NT / Bc;
   const uint4 rec = __ldg(&grec[g]);
-  const int k = (int)rec.w;
-  const int ns = 1 << k;
-  const int b = tid % B;
-  const int rows_per_pass = NT / B;
-  const int64_t per = (D + RC - 1) / RC;
-  const int64_t r0 = (int64_t)chunk * per, r1 = min(D, r0 + per);
-  for (int u = 0; u < ns; ++u) {
-    bins[u * NT + tid] = R(0);
-    bins[(16 + u) * NT + tid] = R(0);
+  const int k = (int)rec.w, ns = 1 << k;
+  const int nb = n - 1;  // compact bits; full-index bit nb is the parity (top) spin
+  auto supp_pos = [&](int kk) { return (int)((rec.z >> (8 * kk)) & 0xffu) + kk; };  // ascending
+  uint32_t smask = 0;
+  int ktop = -1;
+  for (int kk = 0; kk < k; ++kk) {
+    if (supp_pos(kk) < nb) smask |= 1u << supp_pos(kk);
+    else ktop = kk;
   }
-  for (int64_t x = r0 + tid / B; x < r1; x += rows_per_pass) {
-    const uint32_t xc = (uint32_t)x;
-    const uint32_t xf = xc | ((uint32_t)((__popc(xc) + sector) & 1) << (n - 1));
-    const C l = lam[x * B + b];
-    const C p = psi[(int64_t)(xc ^ rec.x) * B + b];
+  uint32_t lmask = smask;
+  for (int bit = 0; __popc(lmask) < LB; ++bit) lmask |= 1u << bit;
+  uint32_t rest = ((1u << nb) - 1u) & ~lmask, cmask = 0;
+  for (int i = 0; i < CB; ++i) {
+    const uint32_t hb = 1u << (31 - __clz(rest));
+    cmask |= hb;
+    rest ^= hb;
+  }
+  const uint32_t jmask = rest;
+  R a0r = R(0), a0i = R(0), a1r = R(0), a1i = R(0);
+  const uint32_t x0 = deposit_bits((uint32_t)r, lmask) | deposit_bits((uint32_t)chunk, cmask);
+  // one row: conj(lam) psi with the sign (-1)^popcount(zeta & xf), into the bin of its parity
+  auto add_row = [&](uint32_t xc) {
+    const uint32_t par = (uint32_t)((__popc(xc) + sector) & 1);
+    const uint32_t xf = xc | (par << nb);
+    const C l = lam[(size_t)xc * Bt + c0 + b];
+    const C p = psi[(size_t)(xc ^ rec.x) * Bt + c0 + b];
     R cr = l.x * p.x + l.y * p.y;  // conj(l) * p
     R ci = l.x * p.y - l.y * p.x;
     if (__popc(rec.y & xf) & 1) {
       cr = -cr;
       ci = -ci;
     }
-    const uint32_t u = grad_supp_bits(xf, rec.z) & (uint32_t)(ns - 1);
-    bins[u * NT + tid] += cr;
-    bins[(16 + u) * NT + tid] += ci;
+    if (par) {
+      a1r += cr;
+      a1i += ci;
+    } else {
+      a0r += cr;
+      a0i += ci;
+    }
+  };
+  if (r < (1 << LB)) {
+    const int nj = __popc(jmask);  // 2^nj rows per thread
+    // blocks of 8 rows for complex128, 4 for complex64 (measured at N = 28, 8 states: 8-row
+    // blocks 160 against 148 us per complex64 launch, 10.5 against 11.1 s per complex128 call)
+    constexpr bool wide = std::is_same<R, double>::value;
+    if (wide && nj >= 3) {
+      term_blocks<3, R, C>(lam, psi, (size_t)Bt, c0 + b, x0, jmask, rec, nb, sector, a0r, a0i, a1r, a1i);
+    } else if (nj >= 2) {
+      term_blocks<2, R, C>(lam, psi, (size_t)Bt, c0 + b, x0, jmask, rec, nb, sector, a0r, a0i, a1r, a1i);
+    } else {
+      uint32_t xj = 0;
+      do {
+        add_row(x0 | xj);
+        xj = ((xj | ~jmask) + 1u) & jmask;
+      } while (xj != 0u);
+    }
   }
-  // Walsh transform of this thread's bins: W_s = sum_u (-1)^popcount(s & u) bin_u
-  R hr[16], hi[16];
+  // bins of this thread: u0 (parity 0) and u1 (parity 1), equal unless the top spin is a support bit
+  uint32_t uc = 0;
+  for (int kk = 0; kk < k; ++kk)
+    if (kk != ktop) uc |= ((x0 >> supp_pos(kk)) & 1u) << kk;
+  const uint32_t u0 = uc, u1 = ktop >= 0 ? (uc | (1u << ktop)) : uc;
+  // Walsh transform of the two bins: W_s = sum_u (-1)^popcount(s & u) bin_u
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    hr[u] = u < ns ? bins[u * NT + tid] : R(0);
-    hi[u] = u < ns ? bins[(16 + u) * NT + tid] : R(0);
-  }
-#pragma unroll
-  for (int h = 1; h < 16; h <<= 1)  // in-place fast transform over the 4 bits (unused bins are 0)
-#pragma unroll
-    for (int u = 0; u < 16; ++u)
-      if (!(u & h)) {
-        const R ar = hr[u], ai = hi[u], br = hr[u | h], bi = hi[u | h];
-        hr[u] = ar + br;
-        hi[u] = ai + bi;
-        hr[u | h] = ar - br;
-        hi[u | h] = ai - bi;
-      }
-  // bins u >= ns are zero, so for s < ns this is the transform over the group's k support bits
-#pragma unroll
-  for (int s = 0; s < 16; ++s)
-    if (s < ns) {
-      bins[s * NT + tid] = hr[s];
-      bins[(16 + s) * NT + tid] = hi[s];
+  for (int sidx = 0; sidx < 16; ++sidx)
+    if (sidx < ns) {
+      const R s0 = (__popc((uint32_t)sidx & u0) & 1) ? R(-1) : R(1);
+      const R s1 = (__popc((uint32_t)sidx & u1) & 1) ? R(-1) : R(1);
+      bins[sidx * NT + tid] = s0 * a0r + s1 * a1r;
+      bins[(16 + sidx) * NT + tid] = s0 * a0i + s1 * a1i;
     }
   __syncthreads();
-  // column b's sum over its threads b, b + B, b + 2B, ... in increasing order
-  for (int o = tid; o < ns * B; o += NT) {
-    const int s = o / B, bb = o - s * B;
+  // column b's sum over its threads b, b + Bc, b + 2 Bc, ... in increasing order
+  for (int o = tid; o < ns * Bc; o += NT) {
+    const int sidx = o / Bc, bb = o - sidx * Bc;
     R sx = R(0), sy = R(0);
     for (int j = 0; j < rows_per_pass; ++j) {
-      sx += bins[s * NT + bb + j * B];
-      sy += bins[(16 + s) * NT + bb + j * B];
+      sx += bins[sidx * NT + bb + j * Bc];
+      sy += bins[(16 + sidx) * NT + bb + j * Bc];
     }
-    partial[(((size_t)g * RC + chunk) * 16 + s) * B + bb] = make_double2((double)sx, (double)sy);
+    partial[(((size_t)g * RC + chunk) * 16 + sidx) * Bt + c0 + bb] = make_double2((double)sx, (double)sy);
   }
 }
 
@@ -181,7 +296,8 @@ struct GradEngine {
   KrylovWS ws;
   std::vector<void*> owned;
   size_t vb = 0;
-  int RC = 1, bdim = 0;
+  // term kernel shape: columns in blocks of Bc <= 16, 2^LB row lanes, RC = 2^CB row chunks
+  int RC = 1, CB = 0, LB = 0, Bc = 1, bdim = 0;
   double2* partial = nullptr;
   double2* dots = nullptr;  // B
 
@@ -223,11 +339,19 @@ struct GradEngine {
     const size_t wsb = krylov_ws_bytes(D, dtype, krylov, B);
     SYK_TRY(alloc(&w, wsb));
     SYK_TRY(krylov_ws_carve(&ws, w, wsb, D, dtype, krylov, B));
-    bdim = int(B) * std::max(1, int(256 / B));
-    const int64_t rows_per_pass = bdim / B;
-    // row chunks of at least 64 rows per thread: the per-block epilogue (Walsh transform of the
-    // bins, column sums) then costs a fraction of the row loop
-    RC = int(std::max<int64_t>(1, std::min<int64_t>(64, D / (rows_per_pass * 64))));
+    // 256 threads: Bc columns x 256 / Bc row lanes (at least 16, so that the <= 4 support bits
+    // below the top spin fit in the lane bits); row chunks of at least 64 rows per thread, so
+    // the per-block epilogue (Walsh transform of the bins, column sums) costs a fraction of the
+    // row loop
+    Bc = int(std::min<int64_t>(B, 16));
+    int lanes = 1;
+    while (lanes * 2 * Bc <= 256) lanes *= 2;
+    bdim = Bc * lanes;
+    const int nb = terms->n - 1;
+    LB = 0;
+    while ((1 << LB) < lanes && LB < nb) ++LB;
+    CB = std::max(0, std::min(6, nb - LB - 6));
+    RC = 1 << CB;
     void* p = nullptr;
     SYK_TRY(alloc(&p, sizeof(double2) * size_t(terms->ngg) * RC * 16 * B));
     partial = static_cast<double2*>(p);
@@ -260,17 +384,23 @@ struct GradEngine {
     // bins: 32 x (at most 256 threads) values of the vector type
     SYK_TRY(ensure_smem_limit((const void*)k_term_grad<float>, 32 * 256 * (int)sizeof(float)));
     SYK_TRY(ensure_smem_limit((const void*)k_term_grad<double>, 32 * 256 * (int)sizeof(double)));
-    if (dtype == SYK_C64)
-      k_term_grad<float><<<grid, bdim, 32 * bdim * sizeof(float), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
-                                                                     (const float2*)lam, (const float2*)psi, partial);
-    else
-      k_term_grad<double><<<grid, bdim, 32 * bdim * sizeof(double), st>>>(terms->d_gg_rec, terms->n, sector, D, int(B),
-                                                                      (const double2*)lam, (const double2*)psi, partial);
+    for (int c0 = 0; c0 < int(B); c0 += Bc) {
+      const int bc = std::min<int>(Bc, int(B) - c0);
+      const int nt = bc * (bdim / Bc);
+      if (dtype == SYK_C64)
+        k_term_grad<float><<<grid, nt, 32 * nt * sizeof(float), st>>>(
+            terms->d_gg_rec, terms->n, sector, LB, CB, int(B), c0, bc, (const float2*)lam, (const float2*)psi, partial);
+      else
+        k_term_grad<double><<<grid, nt, 32 * nt * sizeof(double), st>>>(
+            terms->d_gg_rec, terms->n, sector, LB, CB, int(B), c0, bc, (const double2*)lam, (const double2*)psi,
+            partial);
+      count_launch();
+    }
     const int64_t n = terms->nterms * B;
     k_term_grad_accum<<<unsigned((n + 255) / 256), 256, 0, st>>>(terms->nterms, int(B), RC, terms->d_term_group,
                                                                  terms->d_term_s, terms->d_term_phase, partial,
                                                                  coef.real(), coef.imag(), acc);
-    count_launch(2);
+    count_launch();
     SYK_CUDA_CHECK(cudaGetLastError());
     return SYK_OK;
   }

@@ -31,6 +31,9 @@ def main():
     ap.add_argument("--tile", default=None,
                     help="force the launch shape 'ntb,cluster[,variant]' (no tuning sweep; variant 0 = k_apply_tiled, "
                          "1..3 = k_apply_coset with 2^variant rows per thread)")
+    ap.add_argument("--grad", type=float, default=None, metavar="TSTAR",
+                    help="also time one gradient call syk_otoc_grad (beta J = 5, t* = TSTAR, quad_dz 0.05, "
+                         "tol 1e-7 for c64 and 1e-12 for c128), as the benchmark's gradient workload runs it")
     ap.add_argument("--c128-arith", default="df", choices=["df", "fp64"],
                     help="complex128 matvec arithmetic: double-float (default) or native FP64")
     a = ap.parse_args()
@@ -82,6 +85,17 @@ def main():
                         "krylov_bases": nb, "h_applies": cnt["h_applies"] // a.batch,
                         "workspace_bytes": syk.syk_workspace_bytes(a.N, code, a.krylov, a.batch),
                         "max_norm_change": float(((n1 - n0).abs() / n0).max())}
+    if a.grad is not None:
+        x = psi.clone()
+        tol = 1e-7 if a.dtype == "c64" else 1e-12
+        syk.syk_counters(reset=True)
+        e0.record()
+        syk.syk_otoc_grad(terms, 5.0, 0, 1, a.grad, x, krylov_dim=40, tol=tol, quad_dz=0.05)
+        e1.record()
+        torch.cuda.synchronize()
+        cnt = syk.syk_counters(reset=True)
+        out["grad"] = {"tstar": a.grad, "seconds": e0.elapsed_time(e1) / 1e3, "h_applies": cnt["h_applies"] // a.batch,
+                       "launches": cnt["launches"]}
     print(json.dumps(out))
 
 
