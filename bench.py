@@ -69,6 +69,11 @@ def parse():
     ap.add_argument("--orth", default="default", choices=["default", "full", "local"],
                     help="Lanczos orthogonalisation of the evolutions (library default, full Gram-Schmidt, or the "
                          "three-term recurrence)")
+    ap.add_argument("--n32-curves", action="store_true",
+                    help="the N=32 curve workload at its own size: F~(t) for W=chi_1, V=chi_2 at beta J=10, "
+                         "t in [0, 15] step 0.05 (301 points), 16 states per coupling draw, Krylov 40, in c64 "
+                         "and c128, with the per-curve c64 error against c128")
+    ap.add_argument("--seeds", type=int, default=4, help="coupling draws of the --n32-curves workload")
     ap.add_argument("--no-batched-extra", action="store_true",
                     help="skip the mixed-N batch figure that the default line carries")
     return ap.parse_args()
@@ -608,6 +613,58 @@ def grad_main(a, rank, world, local_rank):
                             "dbeta": rel(res["c64"]["db"], ref["db"])}}), flush=True)
 
 
+def n32_main(a, rank, world, local_rank):
+    """N=32 curve workload at its own size: 301-point F~(t) curves of 16 states per coupling
+    draw in c64 (FP64 Lanczos scalars) and c128, each draw's two calls timed with CUDA events;
+    reports curves/hour of both forms and the largest c64 curve error against c128."""
+    import torch
+
+    from paper_2002_05725_gb300 import inputs, syk
+    torch.cuda.set_device(local_rank)
+    syk.load()
+    N, beta, states = 32, 10.0, 16
+    times = [round(0.05 * k, 12) for k in range(301)]
+    sec = {"c64": 0.0, "c128": 0.0}
+    applies = {"c64": 0, "c128": 0}
+    errs = []
+    for d in range(a.seeds):
+        seed = 1000 * rank + d
+        terms = syk.syk_build_terms(N, inputs.couplings(N, seed=seed))
+        psi = inputs.random_states(N, states, seed=seed)
+        F = {}
+        for dt, tol in (("c64", 1e-7), ("c128", 1e-12)):
+            code = syk.SYK_C64 if dt == "c64" else syk.SYK_C128
+            if d == 0:
+                syk.syk_autotune_apply(terms, code, states)
+            x = torch.from_numpy(np.ascontiguousarray(psi.T)).to(
+                torch.complex64 if dt == "c64" else torch.complex128).cuda()
+            syk.syk_counters(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            F[dt] = syk.syk_otoc(terms, beta, 0, 1, times, x, krylov_dim=40, tol=tol)
+            e1.record()
+            torch.cuda.synchronize()
+            sec[dt] += e0.elapsed_time(e1) / 1e3
+            applies[dt] += syk.syk_counters(reset=True)["h_applies"] // states
+        errs.append(curve_error(F["c64"], F["c128"]))
+    if rank == 0:
+        n = world * a.seeds * states
+        print(json.dumps({
+            "metric": "OTOC curves/hour at N=32 (301 points to t=15), c64 vs c128",
+            "value": n * 3600.0 / sec["c64"], "unit": "curves/hour", "n_gpus": world, "steps": a.seeds,
+            "warmup": 0, "ms_per_step": sec["c64"] * 1e3 / a.seeds, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"regularized OTOC F~(t), N=32 (sector dim 2^15), beta*J={beta:g}, W=chi_0 "
+                                   f"V=chi_1, t in [0, 15] step 0.05 (301 points), {states} Gaussian random states "
+                                   f"per draw, {a.seeds} coupling draws, Krylov dim 40, tol 1e-7 (c64) / 1e-12 (c128)",
+                       "N": N, "seeds": a.seeds, "states_per_draw": states},
+            "c128": {"value": n * 3600.0 / sec["c128"], "seconds": sec["c128"],
+                     "applies_per_curve": applies["c128"] / a.seeds},
+            "c64_seconds": sec["c64"], "c64_applies_per_curve": applies["c64"] / a.seeds,
+            "accuracy": {"max_t_rel_err_c64_vs_c128_per_draw": errs, "max": max(errs)}}), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -623,6 +680,9 @@ def main():
         return
     if a.grad:
         grad_main(a, rank, world, local_rank)
+        return
+    if a.n32_curves:
+        n32_main(a, rank, world, local_rank)
         return
     if world > 1:
         import torch
