@@ -22,6 +22,11 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -286,14 +291,76 @@ struct Op {
 const double kGLx[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
 const double kGLw[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
 
+// One host thread that runs submitted jobs (here: forward Krylov evolutions on the engine's
+// second stream) one at a time.  It lives as long as its engine, so the evolutions' graph
+// cache, which is kept per host thread, survives from one segment to the next.
+struct Worker {
+  std::thread th;
+  std::mutex m;
+  std::condition_variable cv;
+  std::function<int()> job;
+  bool has = false, done = true, quit = false;
+  int rc = SYK_OK;
+  std::string err;
+
+  void start(int dev) {
+    th = std::thread([this, dev] {
+      cudaSetDevice(dev);
+      for (;;) {
+        std::unique_lock<std::mutex> lk(m);
+        cv.wait(lk, [&] { return has || quit; });
+        if (quit) return;
+        std::function<int()> f = std::move(job);
+        has = false;
+        lk.unlock();
+        const int r = f();
+        std::string e = r != SYK_OK ? std::string(syk_last_error()) : std::string();
+        lk.lock();
+        rc = r;
+        err = std::move(e);
+        done = true;
+        cv.notify_all();
+      }
+    });
+  }
+  void submit(std::function<int()> f) {
+    std::lock_guard<std::mutex> lk(m);
+    job = std::move(f);
+    has = true;
+    done = false;
+    cv.notify_all();
+  }
+  // waits for the submitted job; returns its code (message in *e)
+  int wait(std::string* e) {
+    std::unique_lock<std::mutex> lk(m);
+    cv.wait(lk, [&] { return done; });
+    *e = err;
+    return rc;
+  }
+  void stop() {
+    {
+      std::lock_guard<std::mutex> lk(m);
+      quit = true;
+    }
+    cv.notify_all();
+    if (th.joinable()) th.join();
+  }
+};
+
 struct GradEngine {
   const syk_terms* terms = nullptr;
   int dtype = 0, krylov = 0;
   int64_t B = 0, D = 0;
   double beta = 0, t = 0, tol = 0, rho = 1.0, dz = 0.05;  // dz: max |z| per sub-interval
   cudaStream_t st = nullptr;
+  // the forward evolutions of the backward sweep run on st2 (own workspace ws2, driven from a
+  // second host thread) while the adjoint evolution of the same segment runs on st
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_fwd = nullptr;
+  int device = 0;
+  Worker worker;
   ApplyParams P[2];
-  KrylovWS ws;
+  KrylovWS ws, ws2;
   std::vector<void*> owned;
   size_t vb = 0;
   // term kernel shape: columns in blocks of Bc <= 16, 2^LB row lanes, RC = 2^CB row chunks
@@ -302,6 +369,13 @@ struct GradEngine {
   double2* dots = nullptr;  // B
 
   ~GradEngine() {
+    worker.stop();
+    if (st2) {
+      cudaStreamSynchronize(st2);  // ws2 and node vectors are freed on st below
+      cudaStreamDestroy(st2);
+    }
+    if (ev_main) cudaEventDestroy(ev_main);
+    if (ev_fwd) cudaEventDestroy(ev_fwd);
     for (void* p : owned) cudaFreeAsync(p, st);
   }
   int alloc(void** p, size_t bytes) {
@@ -339,6 +413,13 @@ struct GradEngine {
     const size_t wsb = krylov_ws_bytes(D, dtype, krylov, B);
     SYK_TRY(alloc(&w, wsb));
     SYK_TRY(krylov_ws_carve(&ws, w, wsb, D, dtype, krylov, B));
+    SYK_TRY(alloc(&w, wsb));
+    SYK_TRY(krylov_ws_carve(&ws2, w, wsb, D, dtype, krylov, B));
+    SYK_CUDA_CHECK(cudaGetDevice(&device));
+    SYK_CUDA_CHECK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    SYK_CUDA_CHECK(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
+    SYK_CUDA_CHECK(cudaEventCreateWithFlags(&ev_fwd, cudaEventDisableTiming));
+    worker.start(device);
     // 256 threads: Bc columns x 256 / Bc row lanes (at least 16, so that the <= 4 support bits
     // below the top spin fit in the lane bits); row chunks of at least 64 rows per thread, so
     // the per-block epilogue (Walsh transform of the bins, column sums) costs a fraction of the
@@ -465,7 +546,16 @@ struct GradEngine {
       // forward nodes, ascending: sub-interval s, node q at fraction ((s - s0) + (1 + x_q)/2) / L
       for (int s = s0; s < s1; ++s)
         for (int q = 0; q < 4; ++q) frf[(s - s0) * 4 + q] = ((s - s0) + 0.5 * (1.0 + kGLx[q])) / L;
-      SYK_TRY(expmv_points(sector, zs * double(L), ckpt[sg], frf.data(), 4 * L, nodeF.data()));
+      // forward nodes on st2, after everything st has queued (the checkpoint, and the previous
+      // segment's term kernels that read nodeF), from a second host thread: its convergence
+      // checks then do not hold up the adjoint evolution below
+      SYK_CUDA_CHECK(cudaEventRecord(ev_main, st));
+      SYK_CUDA_CHECK(cudaStreamWaitEvent(st2, ev_main, 0));
+      const std::complex<double> zf = zs * double(L);
+      void* const ck = ckpt[sg];
+      worker.submit([this, sector, zf, ck, L, &frf, &nodeF] {
+        return syk::expmv_points(P[sector], dtype, zf, ck, frf.data(), 4 * L, nodeF.data(), B, tol, ws2, st2);
+      });
       // adjoint nodes by increasing distance from s1/S (s = s1-1 .. s0, q = 3 .. 0), then v = s0/S
       int k = 0;
       for (int s = s1 - 1; s >= s0; --s)
@@ -476,7 +566,16 @@ struct GradEngine {
         }
       fra[k] = 1.0;
       outa[k] = lam;
-      SYK_TRY(expmv_points(sector, zbar * (double(L) / S), lam, fra.data(), k + 1, outa.data()));
+      const int rc_a = expmv_points(sector, zbar * (double(L) / S), lam, fra.data(), k + 1, outa.data());
+      std::string err_f;
+      const int rc_f = worker.wait(&err_f);
+      if (rc_f != SYK_OK) {
+        set_error("%s", err_f.c_str());
+        return rc_f;
+      }
+      SYK_TRY(rc_a);
+      SYK_CUDA_CHECK(cudaEventRecord(ev_fwd, st2));
+      SYK_CUDA_CHECK(cudaStreamWaitEvent(st, ev_fwd, 0));
       for (int s = s1 - 1; s >= s0; --s)
         for (int q = 3; q >= 0; --q)
           SYK_TRY(term_grad(sector, nodeA[(s - s0) * 4 + q], nodeF[(s - s0) * 4 + q], z * (0.5 * kGLw[q] / S), gJ));
