@@ -53,6 +53,29 @@ def test_df_apply_full_vs_oracle_and_fp64(torch, N, B):
         assert rel(y64, ref) < 1e-14
 
 
+def test_df_one_state_every_launch_shape(torch):
+    """One complex128 state: the double-float tiled kernel at every CTA width and cluster size,
+    full H at N = 24 (sector 2^11: 8, 4 or 2 tiles of 4 rows per thread), both sectors, against
+    the FP64 oracle."""
+    N = 24
+    J = inputs.couplings(N, 32)
+    terms = syk.syk_build_terms(N, J)
+    psi = inputs.random_states(N, 1, 301)
+    x = to_dev(torch, psi, "c128")
+    try:
+        for sector in (0, 1):
+            ref = hm.H_sector_sparse(N, J, sector) @ psi.T
+            for ntb in (6, 7, 8):
+                for cs in (1, 2, 4, 8):
+                    syk.syk_autotune_import('{"apply_tiles": [{"N": %d, "dtype": %d, "batch": 1, "ntb": %d, '
+                                            '"cluster": %d}]}' % (N, syk.SYK_C128, ntb, cs))
+                    y, mv = _apply(terms, sector, x, syk.C128_DOUBLE_FLOAT)
+                    assert mv["tiled"] == 1 and mv["rows"] == 0, (ntb, cs, mv)
+                    assert rel(y, ref) < DF_TOL, (sector, ntb, cs, rel(y, ref))
+    finally:
+        syk.syk_autotune_reset()
+
+
 @pytest.mark.parametrize("B", [1, 16])
 def test_df_apply_sampled_rows_N40(torch, B):
     """N = 40 (sector 2^19, 5036 X-masks per row): sampled rows against the oracle's
