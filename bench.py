@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--batched-Ns", default="20,24,28,32,36,40", help="sizes of the --batched workload")
     ap.add_argument("--graphs", default="segments", choices=["off", "segments", "device"],
                     help="launch mode of the Krylov evolutions of the --batched workload (syk_use_graphs 0/1/2)")
+    ap.add_argument("--persistent", default="on", choices=["on", "off"],
+                    help="run the --batched items that fit one CTA in the persistent launch (on) or every item on "
+                         "the per-item streams (off)")
     ap.add_argument("--grad", action="store_true",
                     help="gradient workload: dF~(t*)/dJ for all couplings and dF~/dbeta at N=28, beta J=5, "
                          "t*=5, about 200 quadrature sub-intervals, 8 states, c64 and c128")
@@ -522,6 +525,7 @@ def run_batched(a, rank, world, local_rank, draws):
     times = time_grid(a.npts, a.tmax)
     Ns, betas = [int(v) for v in a.batched_Ns.split(",")], [1.0, 3.0, 10.0]
     syk.syk_use_graphs({"off": 0, "segments": 1, "device": 2}[a.graphs])
+    prev_persistent = syk.syk_batch_persistent(a.persistent == "on")
     items = []
     for d in range(draws):
         for N in Ns:
@@ -543,17 +547,28 @@ def run_batched(a, rank, world, local_rank, draws):
     wall = time.perf_counter() - t0
     clocks = clk.stop()
     cnt = syk.syk_counters(reset=True)
+    rep = syk.syk_batch_report()
     syk.syk_use_graphs(True)
+    syk.syk_batch_persistent(prev_persistent)
     curves = 8 * len(items)
+    cyc = max(rep["cycles_items"], 1)
+    persistent = {"items": rep["persistent_items"], "per_item_path_items": rep["stream_items"],
+                  "ctas": rep["persistent_ctas"], "h_applies": rep["h_applies"],
+                  "cycle_shares": {"matvec": rep["cycles_matvec"] / cyc, "convergence_checks": rep["cycles_check"] / cyc,
+                                   "full_eigendecompositions": rep["cycles_eig"] / cyc},
+                  "note": "items whose sector vector fits one CTA's shared memory run as one persistent launch "
+                          "(a CTA per item, the whole chain on the device); cycle shares are SM clock cycles "
+                          "summed over those items"}
     return {"metric": "OTOC curves/hour, mixed-N batch", "value": world * curves * 3600.0 / wall,
             "unit": "curves/hour", "wall_s": wall, "dtype": "c64",
             "config": {"workload": f"{draws} draw(s) x N in {Ns} x beta J in {betas}, 8 states each, "
                                    f"F~ at t=0 and {a.npts} points to t={a.tmax:g}, Krylov {a.krylov}, "
-                                   f"tol {a.tol:g}, {a.workers} host workers / streams",
+                                   f"tol {a.tol:g}, {a.workers} host workers / streams for the items outside "
+                                   f"the persistent launch (persistent {a.persistent})",
                        "items": len(items), "curves": curves,
                        "evolutions": {"off": "host-driven, direct launches", "segments": "host-driven, segment graphs",
                                       "device": "device-driven graphs"}[a.graphs]},
-            "clocks": clocks,
+            "clocks": clocks, "persistent": persistent,
             "gpu_launches": cnt["launches"], "h_applies": cnt["h_applies"],
             "result_check": {"Ftilde_t0_all_one": bool(all(np.allclose(F[0] / F[0], 1) for F in out))}}
 

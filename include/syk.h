@@ -232,12 +232,20 @@ int syk_correlator_G_imag(const syk_terms* terms, double beta, int i, const doub
 /* syk_otoc_batch -- the batched workload: many independent OTOC evaluations
  * (coupling draws of any N, each with its beta and its D x nstates random
  * states, device or host memory) at the common times t, Majoranas i, j, dtype
- * and Krylov settings.  Items are taken in order by `nworkers` host threads,
- * each with its own CUDA stream, so that items of small sectors run
- * concurrently; every distinct (N, nstates) is autotuned first.  Each item's
- * F_re_im (host, nt x nstates x 2) is filled as by syk_otoc; item_status (may
- * be NULL) receives each item's return code.  Returns the first failure.
- * The paper averages over hundreds of such draws (Supp. Sec. I.C). */
+ * and Krylov settings.  Items whose whole chain fits one CTA (complex64 with
+ * the three-term Lanczos recurrence, nstates in {1, 2, 4, 8, 16}, the sector
+ * vector of D x nstates values within shared memory: N <= 24 at 8 states)
+ * run as ONE persistent kernel launch (a CUDA graph of the queue reset and
+ * the kernel): each CTA takes items from a device-side queue and evaluates an
+ * item's entire chain -- Lanczos evolutions with FP64 scalars, tridiagonal
+ * eigendecompositions, step control, Majoranas, dots -- with no host round
+ * trip (syk_batch_persistent(0) turns this off).  The other items are taken,
+ * largest first, by `nworkers` host threads, each with its own CUDA stream,
+ * concurrently with that launch; every distinct (N, nstates) of theirs is
+ * autotuned first.  Each item's F_re_im (host, nt x nstates x 2) is filled as
+ * by syk_otoc; item_status (may be NULL) receives each item's return code.
+ * Returns the first failure.  The paper averages over hundreds of such draws
+ * (Supp. Sec. I.C). */
 typedef struct {
   const syk_terms* terms;
   double beta;
@@ -247,6 +255,18 @@ typedef struct {
 } syk_otoc_item;
 int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const double* t, int nt,
                    int dtype, int krylov_dim, double tol, int nworkers, int* item_status);
+/* syk_batch_persistent -- 1 (default): syk_otoc_batch runs the items that fit
+ * one CTA in its persistent launch; 0: every item takes the per-item path.
+ * Returns the previous mode.  Plumbing; no counterpart in the paper. */
+int syk_batch_persistent(int on);
+/* syk_batch_report -- counters of the last syk_otoc_batch call (host array of
+ * n <= 8 words): items in the persistent launch, items on the per-item path,
+ * CTAs of the persistent launch, and, summed over its items, SM clock cycles
+ * spent in matvecs, in convergence checks (tridiagonal eigenvalues and step
+ * selection), in the full eigendecompositions of accepted bases and in whole
+ * items, and H applications (states x matvecs).  Measurement; no counterpart in
+ * the paper. */
+int syk_batch_report(long long* out, int n);
 
 /* --------------------------------------------------------------- gradients
  * syk_otoc_grad -- F~(t) = F(t)/F(0) of syk_otoc at one time t for each state,

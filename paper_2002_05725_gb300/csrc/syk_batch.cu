@@ -1,0 +1,944 @@
+// Persistent batched OTOC: the disorder and random-state average of Supp. Sec. I.C as ONE
+// kernel launch over many small-sector work items.  Each CTA takes items from a device-side
+// queue (an atomic counter) and evaluates an item's whole regularized-OTOC chain (Eq. F_reg
+// by Eq. q_typicality, the chain of syk_otoc) by itself: every Krylov evolution (Supp. Sec.
+// I.B: Lanczos with the three-term recurrence, FP64 scalars, FP64 tridiagonal
+// eigendecompositions, Saad's error estimate and the step control of syk_expmv), the
+// Majorana applications and the final dots.  The item's sector vector fits in shared memory,
+// so every matvec gathers its partner rows psi[x ^ m] from the staged input; the Krylov basis
+// and the chain's vectors live in the CTA's own slice of global memory (L2).  CTAs share
+// nothing but the queue counter: there is no grid-wide synchronisation and no host round
+// trip until the launch ends.  complex64 vectors (FP32 arithmetic), as the batched workload
+// specifies; larger sectors and complex128 items take the per-item path of syk_otoc_batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "syk_krylov.cuh"
+#include "syk_tile.cuh"
+#include "syk_tridiag.cuh"
+
+namespace syk {
+namespace {
+
+constexpr int kPNT = 512;              // threads per CTA
+constexpr int kPWarps = kPNT / 32;     // >= the largest batch of an item (16)
+constexpr int kPG = 64;                // popcount-4 masks staged in shared memory per chunk
+// Bounds on the Krylov bases of one evolution and of one item (a sane chain needs a few per
+// evolution): past them the item stops with error bit 4, so no input keeps a CTA busy for long.
+constexpr int kMaxBasesPerEvolution = 1000;
+constexpr long long kMaxBasesPerItem = 4000;
+
+// One work item: a coupling draw's tables (complex64 copies), its states and beta.
+struct PItem {
+  const uint4* m4_rec;
+  const float2* m4_t32;
+  const uint4* m2_rec;
+  const float2* m2_t32;
+  const float* wd32;
+  const float2* psi0;  // D x B (device)
+  double2* F;          // nt x B results (device)
+  double beta, rho;
+  int n, D, n4, n2;
+  int every;           // Lanczos vectors between two convergence checks after the first
+  int pad;
+};
+
+// Per-item record written by the kernel.
+enum { kStStatus = 0, kStMatvecs = 1, kStBases = 2, kStCyMatvec = 3, kStCyCheck = 4, kStCyEig = 5, kStCyAll = 6,
+       kStWords = 8 };
+
+// Shared-memory layout of a launch (byte offsets, computed on the host).
+struct PLayout {
+  int A;        // region A: staged matvec input | convergence-check scratch | eigenvector matrices
+  int rec, tab;  // staged popcount-4 records and 32-entry tables
+  int alpha, beta, sc, beta0, h, n2, cc, red, sb, fc, ctl;
+  int total;
+  int ncol;     // columns per round of the full eigendecomposition
+};
+
+struct PArgs {
+  const PItem* items;
+  int nitems;
+  int* next;          // queue counter, 0 at launch
+  long long* stat;    // kStWords per item
+  const double* t;    // nt output times (device)
+  int nt, i, j;       // Majoranas i (W), j (V)
+  int m;              // Krylov dimension
+  double tol, bt;     // step tolerance, breakdown threshold of beta_j
+  float2* ws;         // per CTA: (m + 5) vectors of vmax elements
+  long long vmax;
+  PLayout L;
+};
+
+struct PCtl {
+  int item, status, first;
+  double s_acc;
+};
+
+// ---------------------------------------------------------------- row access
+// Rows are B contiguous complex64 values (16-byte aligned for B >= 2), accessed as column
+// pairs: pair q holds columns 2q and 2q + 1 (B >= 2) or column 0 alone (B == 1).
+constexpr int npairs(int B) { return B >= 2 ? B / 2 : 1; }
+template <int B>
+__device__ __forceinline__ void ld_pair(const float2* row, int q, float2& v0, float2& v1) {
+  if constexpr (B == 1) {
+    v0 = row[0];
+    v1 = make_float2(0.f, 0.f);
+  } else {
+    const float4 t = reinterpret_cast<const float4*>(row)[q];
+    v0 = make_float2(t.x, t.y);
+    v1 = make_float2(t.z, t.w);
+  }
+}
+template <int B>
+__device__ __forceinline__ void st_pair(float2* row, int q, float2 v0, float2 v1) {
+  if constexpr (B == 1) row[0] = v0;
+  else reinterpret_cast<float4*>(row)[q] = make_float4(v0.x, v0.y, v1.x, v1.y);
+}
+// p += conj(a) b
+__device__ __forceinline__ void cdot_acc(float2& p, const float2 a, const float2 b) {
+  p.x = fmaf(a.x, b.x, fmaf(a.y, b.y, p.x));
+  p.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, p.y));
+}
+__device__ __forceinline__ void norm_acc(float2& p, const float2 a) { p.x = fmaf(a.x, a.x, fmaf(a.y, a.y, p.x)); }
+
+// ---------------------------------------------------------------- reductions
+// Compensated FP32 sum over the warp (Knuth's TwoSum at every level of the butterfly): the
+// pair (hi, lo) carries the sum to about 2^-44 relative, the same in every lane.
+__device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, oh);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(oh, bp));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, ol), err);
+  }
+}
+
+// out[c] = sum over the CTA of the threads' v[c] (c < B): per-thread FP32 partial sums (of at
+// most 16 rows), a compensated sum per warp, then FP64 over the warps in increasing order
+// (deterministic).  Ends with a barrier, so out is visible to every thread.
+template <int B>
+__device__ void cta_sum_cols(const float2 (&v)[B], double2* red, double2* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    float xh = v[c].x, xl = 0.f, yh = v[c].y, yl = 0.f;
+    df_warp_sum(xh, xl);
+    df_warp_sum(yh, yl);
+    if (lane == 0) red[w * B + c] = make_double2((double)xh + (double)xl, (double)yh + (double)yl);
+  }
+  __syncthreads();
+  if (threadIdx.x < B) {
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < kPWarps; ++k) {
+      sx += red[k * B + threadIdx.x].x;
+      sy += red[k * B + threadIdx.x].y;
+    }
+    out[threadIdx.x] = make_double2(sx, sy);
+  }
+  __syncthreads();
+}
+
+// Shared-memory views of a launch.
+struct PSmem {
+  unsigned char* A;
+  uint4* rec;
+  float2* tab;
+  double *alpha, *beta, *sc, *beta0, *sb;
+  double2 *h, *n2, *cc, *red;
+  // FP32 coefficients of the vector passes, per column c: fc[c] = (sc_j, 0) of the staged
+  // input, fc[B + c] = -h_j, fc[2B + c] = (-beta_{j-1} sc_{j-1}, 0), fc[(3 + k) B + c] =
+  // cc_k sc_k of the combination (written once by a few threads: the FP64 pipe is 1/64 of
+  // the FP32 rate, so no pass converts FP64 scalars per element)
+  float2* fc;
+  PCtl* ctl;
+  __device__ PSmem(unsigned char* base, const PLayout& L)
+      : A(base + L.A),
+        rec(reinterpret_cast<uint4*>(base + L.rec)),
+        tab(reinterpret_cast<float2*>(base + L.tab)),
+        alpha(reinterpret_cast<double*>(base + L.alpha)),
+        beta(reinterpret_cast<double*>(base + L.beta)),
+        sc(reinterpret_cast<double*>(base + L.sc)),
+        beta0(reinterpret_cast<double*>(base + L.beta0)),
+        sb(reinterpret_cast<double*>(base + L.sb)),
+        h(reinterpret_cast<double2*>(base + L.h)),
+        n2(reinterpret_cast<double2*>(base + L.n2)),
+        cc(reinterpret_cast<double2*>(base + L.cc)),
+        red(reinterpret_cast<double2*>(base + L.red)),
+        fc(reinterpret_cast<float2*>(base + L.fc)),
+        ctl(reinterpret_cast<PCtl*>(base + L.ctl)) {}
+};
+
+// ---------------------------------------------------------------- vector passes
+// Thread t handles rows t, t + kPNT, ... (all B columns of each).
+
+// out[c] = sum_x conj(x[x][c]) y[x][c]
+template <int B>
+__device__ __noinline__ void cta_dot(const float2* x, const float2* y, int D, PSmem& S, double2* out) {
+  float2 p[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) p[c] = make_float2(0.f, 0.f);
+  for (int r = threadIdx.x; r < D; r += kPNT) {
+#pragma unroll
+    for (int q = 0; q < npairs(B); ++q) {
+      float2 a0, a1, b0, b1;
+      ld_pair<B>(x + (size_t)r * B, q, a0, a1);
+      ld_pair<B>(y + (size_t)r * B, q, b0, b1);
+      cdot_acc(p[B >= 2 ? 2 * q : 0], a0, b0);
+      if constexpr (B >= 2) cdot_acc(p[2 * q + 1], a1, b1);
+    }
+  }
+  cta_sum_cols<B>(p, S.red, out);
+}
+
+// y = x (elementwise copy)
+template <int B>
+__device__ void cta_copy(const float2* x, float2* y, int D) {
+  for (int r = threadIdx.x; r < D; r += kPNT) {
+#pragma unroll
+    for (int q = 0; q < npairs(B); ++q) {
+      float2 a0, a1;
+      ld_pair<B>(x + (size_t)r * B, q, a0, a1);
+      st_pair<B>(y + (size_t)r * B, q, a0, a1);
+    }
+  }
+  __syncthreads();
+}
+
+// y = chi_maj x (Supp. Sec. I.A): x in sector 1 - sector_out, y in sector_out; as k_apply_chi
+template <int B>
+__device__ __noinline__ void cta_chi(int n, int D, int maj, int sector_out, const float2* x, float2* y) {
+  const int k = maj >> 1;
+  const float hh = 0.70710678118654752440f;
+  for (int r = threadIdx.x; r < D; r += kPNT) {
+    const uint32_t co = (uint32_t)r;
+    const uint32_t xo = co | ((uint32_t)((__popc(co) + sector_out) & 1) << (n - 1));
+    const uint32_t xs = xo ^ (1u << k);
+    const float sg = (__popc(xs & ((1u << k) - 1u)) & 1) ? -hh : hh;
+    const float2* src = x + (size_t)(xs & (uint32_t)(D - 1)) * B;
+    const float si = ((xs >> k) & 1u) ? -sg : sg;  // odd maj: +i (x_k = 0) or -i (x_k = 1)
+#pragma unroll
+    for (int q = 0; q < npairs(B); ++q) {
+      float2 v0, v1;
+      ld_pair<B>(src, q, v0, v1);
+      if (maj & 1) {
+        v0 = make_float2(-si * v0.y, si * v0.x);
+        v1 = make_float2(-si * v1.y, si * v1.x);
+      } else {
+        v0 = make_float2(sg * v0.x, sg * v0.y);
+        v1 = make_float2(sg * v1.x, sg * v1.y);
+      }
+      st_pair<B>(y + (size_t)r * B, q, v0, v1);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- matvec
+// y = H xs in sector `sector` (Supp. Sec. I.B; the sums of k_apply_rows), xs staged in shared
+// memory (D x B).  A thread owns RPT rows r0 + tid + i kPNT of each pass and all B columns;
+// rows wider than 16 bytes are read in 16-byte chunks in a lane-rotated order (chunk
+// (q + lane) mod Q into accumulator q) so that the 32 lanes of a warp hit distinct banks.  The
+// popcount-4 records and tables are staged in chunks of kPG masks.
+template <int B, int RPT>
+__device__ __noinline__ void cta_matvec(const PItem& it, int sector, const float2* __restrict__ xs, float2* __restrict__ y,
+                           PSmem& S) {
+  constexpr int Q = B >= 2 ? B / 2 : 1;
+  using V = typename std::conditional<(B >= 2), float4, float2>::type;
+  const int tid = threadIdx.x;
+  const int rot = (tid & 31) & (Q - 1);
+  const int n = it.n, D = it.D;
+  const V* __restrict__ x4 = reinterpret_cast<const V*>(xs);
+  auto mac = [](V& a, float cr, float ci, const V v) {
+    if constexpr (B >= 2) {
+      Slot<float>::mac(a, cr, ci, v);
+    } else {
+      cmac(a, cr, ci, v);
+    }
+  };
+  for (int r0 = 0; r0 < D; r0 += kPNT * RPT) {
+    uint32_t xr[RPT], xf[RPT];
+    bool ok[RPT];
+    V acc[RPT][Q];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = r0 + tid + i * kPNT;
+      ok[i] = r < D;
+      xr[i] = (uint32_t)(ok[i] ? r : 0);
+      xf[i] = xr[i] | ((uint32_t)((__popc(xr[i]) + sector) & 1) << (n - 1));
+      if (!ok[i]) continue;
+      const float c0 = diag_coef<float>(it.wd32, n, xf[i]);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const V v = x4[xr[i] * Q + ((q + rot) & (Q - 1))];
+        if constexpr (B >= 2) acc[i][q] = make_float4(c0 * v.x, c0 * v.y, c0 * v.z, c0 * v.w);
+        else acc[i][q] = make_float2(c0 * v.x, c0 * v.y);
+      }
+      for (int k = 0; k < it.n2; ++k) {
+        const uint4 rec = __ldg(&it.m2_rec[k]);
+        float cr, ci;
+        pc2_coef<float2, float>(it.m2_t32, k, n, rec, xf[i], cr, ci);
+        const uint32_t pr = xr[i] ^ rec.x;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) mac(acc[i][q], cr, ci, x4[pr * Q + ((q + rot) & (Q - 1))]);
+      }
+    }
+    for (int c0 = 0; c0 < it.n4; c0 += kPG) {
+      const int cnt = min(kPG, it.n4 - c0);
+      __syncthreads();  // the previous chunk's records and tables are no longer read
+      for (int e = tid; e < cnt; e += kPNT) S.rec[e] = __ldg(&it.m4_rec[c0 + e]);
+      const float4* src = reinterpret_cast<const float4*>(it.m4_t32 + (size_t)c0 * 32);
+      float4* dst = reinterpret_cast<float4*>(S.tab);
+      for (int e = tid; e < cnt * 16; e += kPNT) dst[e] = __ldg(&src[e]);
+      __syncthreads();
+      for (int k = 0; k < cnt; ++k) {
+        const uint4 rec = S.rec[k];
+        const float2* T = S.tab + k * 32;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          if (!ok[i]) continue;
+          const uint32_t idx = supp_bits(xf[i], rec.z) | ((__popc(rec.y & xf[i]) & 1u) << 4);
+          const float2 cf = T[idx];
+          const uint32_t pr = xr[i] ^ rec.x;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) mac(acc[i][q], cf.x, cf.y, x4[pr * Q + ((q + rot) & (Q - 1))]);
+        }
+      }
+    }
+    V* y4 = reinterpret_cast<V*>(y);
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      if (!ok[i]) continue;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) y4[xr[i] * Q + ((q + rot) & (Q - 1))] = acc[i][q];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ long long clk() { return clock64(); }
+
+// ---------------------------------------------------------------- one evolution
+// out = e^{z H} in in sector `sector` (in and out may alias), with the step control of
+// syk_expmv for one output (expmv_T with a single fraction 1): Krylov bases of up to m vectors,
+// convergence checks by the plan of check_plan (first check at 3/4 of the predicted
+// dimension, later ones every it.every vectors; restarts from 4 vectors on), the largest step
+// per basis whose estimate is <= tol for every column, restarts from the end state.
+// basis: slots 1..m of the Krylov basis (slot k at basis + (k-1) vmax); slot 0 is `in` or the
+// restart state.  Error bits go to S.ctl->status (1 non-finite scalar, 2 eigensolver, 4 step
+// collapse or too many bases).
+template <int B, int RPT>
+__device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sector, double zr, double zi, const float2* in,
+                          float2* out, float2* basis, PSmem& S, long long* cy, long long& mv, long long& nb) {
+  const int D = it.D, m = a.m, tid = threadIdx.x;
+  const double tol = a.tol;
+  if (zr == 0.0 && zi == 0.0) {
+    if (out != in) cta_copy<B>(in, out, D);
+    return;
+  }
+  if (tid == 0) {  // predicted Krylov dimension: smallest k with (e rho |z| / 2k)^k <= tol
+    const double rt = hypot(zr, zi) * it.rho;
+    int k = m + 1;
+    for (int kk = 1; kk <= m; ++kk)
+      if (rt <= 0.0 || double(kk) * log(2.718281828459045 * rt / (2.0 * kk)) <= log(tol)) {
+        k = kk;
+        break;
+      }
+    S.ctl->first = min(m, max(4, (3 * k) / 4));
+  }
+  __syncthreads();
+  const int first = S.ctl->first;
+  double s_rem = 1.0, s_done = 0.0;
+  const float2* cur = in;
+  float2* xs = reinterpret_cast<float2*>(S.A);
+  int bases = 0;
+  while (s_rem > 0.0) {
+    if (++bases > kMaxBasesPerEvolution || nb >= kMaxBasesPerItem) {
+      if (tid == 0) S.ctl->status |= 4;
+      __syncthreads();
+      return;
+    }
+    ++nb;
+    auto U = [&](int k) -> const float2* { return k == 0 ? cur : basis + (size_t)(k - 1) * a.vmax; };
+    // beta0 = ||cur||, sc_0 = 1/beta0
+    {
+      float2 p[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) p[c] = make_float2(0.f, 0.f);
+      for (int r = tid; r < D; r += kPNT) {
+#pragma unroll
+        for (int q = 0; q < npairs(B); ++q) {
+          float2 v0, v1;
+          ld_pair<B>(cur + (size_t)r * B, q, v0, v1);
+          norm_acc(p[B >= 2 ? 2 * q : 0], v0);
+          if constexpr (B >= 2) norm_acc(p[2 * q + 1], v1);
+        }
+      }
+      cta_sum_cols<B>(p, S.red, S.n2);
+      if (tid < B) {
+        const double nb0 = sqrt(fmax(S.n2[tid].x, 0.0));
+        if (!isfinite(nb0)) atomicOr(&S.ctl->status, 1);
+        S.beta0[tid] = nb0;
+        S.sc[tid] = nb0 > 0.0 ? 1.0 / nb0 : 0.0;
+        S.fc[tid] = make_float2((float)S.sc[tid], 0.f);
+      }
+      __syncthreads();
+    }
+    int j0 = 0, m_eff = m;
+    int j1 = bases == 1 ? first : min(m, 4);
+    double s_acc = 0.0;
+    for (;;) {
+      for (int j = j0; j < j1; ++j) {
+        // stage v_j = sc_j u_j
+        {
+          const float2* u = U(j);
+          for (int r = tid; r < D; r += kPNT) {
+#pragma unroll
+            for (int q = 0; q < npairs(B); ++q) {
+              float2 v0, v1;
+              ld_pair<B>(u + (size_t)r * B, q, v0, v1);
+              const float s0 = S.fc[B >= 2 ? 2 * q : 0].x;
+              const float s1 = B >= 2 ? S.fc[2 * q + 1].x : 0.f;
+              st_pair<B>(xs + (size_t)r * B, q, make_float2(v0.x * s0, v0.y * s0), make_float2(v1.x * s1, v1.y * s1));
+            }
+          }
+          __syncthreads();
+        }
+        float2* w = basis + (size_t)j * a.vmax;  // slot j+1
+        const long long t0 = clk();
+        cta_matvec<B, RPT>(it, sector, xs, w, S);
+        cy[0] += clk() - t0;
+        ++mv;
+        // h_j = <v_j, w>
+        cta_dot<B>(xs, w, D, S, S.h);
+        if (tid < B) {
+          S.fc[B + tid] = make_float2((float)(-S.h[tid].x), (float)(-S.h[tid].y));
+          S.fc[2 * B + tid] =
+              make_float2(j > 0 ? (float)(-S.beta[(j - 1) * B + tid] * S.sc[(j - 1) * B + tid]) : 0.f, 0.f);
+        }
+        __syncthreads();
+        // u_{j+1} = w - h_j v_j - beta_{j-1} v_{j-1}, |u_{j+1}|^2
+        {
+          const float2* vm = j > 0 ? U(j - 1) : nullptr;
+          float2 p[B];
+#pragma unroll
+          for (int c = 0; c < B; ++c) p[c] = make_float2(0.f, 0.f);
+          for (int r = tid; r < D; r += kPNT) {
+#pragma unroll
+            for (int q = 0; q < npairs(B); ++q) {
+              float2 w0, w1, v0, v1;
+              ld_pair<B>(w + (size_t)r * B, q, w0, w1);
+              ld_pair<B>(xs + (size_t)r * B, q, v0, v1);
+              const int c0 = B >= 2 ? 2 * q : 0, c1 = B >= 2 ? 2 * q + 1 : 0;
+              const float2 h0 = S.fc[B + c0], h1 = S.fc[B + c1];
+              cmac(w0, h0.x, h0.y, v0);
+              cmac(w1, h1.x, h1.y, v1);
+              if (vm) {
+                float2 p0, p1;
+                ld_pair<B>(vm + (size_t)r * B, q, p0, p1);
+                const float f0 = S.fc[2 * B + c0].x, f1 = S.fc[2 * B + c1].x;
+                w0 = make_float2(fmaf(f0, p0.x, w0.x), fmaf(f0, p0.y, w0.y));
+                w1 = make_float2(fmaf(f1, p1.x, w1.x), fmaf(f1, p1.y, w1.y));
+              }
+              st_pair<B>(w + (size_t)r * B, q, w0, w1);
+              norm_acc(p[c0], w0);
+              if constexpr (B >= 2) norm_acc(p[c1], w1);
+            }
+          }
+          cta_sum_cols<B>(p, S.red, S.n2);
+        }
+        // alpha_j, beta_j (breakdown: beta_j = 0), sc_{j+1} = 1/beta_j, as k_lanczos_scalars
+        if (tid < B) {
+          const int c = tid;
+          const double al = S.h[c].x;
+          double be = sqrt(fmax(S.n2[c].x, 0.0));
+          if (!isfinite(al) || !isfinite(be)) {
+            atomicOr(&S.ctl->status, 1);
+            be = 0.0;
+          }
+          const double prev = j > 0 ? S.beta[(j - 1) * B + c] : 0.0;
+          if (be <= a.bt * (fabs(al) + prev)) be = 0.0;
+          S.alpha[j * B + c] = isfinite(al) ? al : 0.0;
+          S.beta[j * B + c] = be;
+          S.sc[(j + 1) * B + c] = be > 0.0 ? 1.0 / be : 0.0;
+          S.fc[c] = make_float2((float)S.sc[(j + 1) * B + c], 0.f);  // the next step's staging
+        }
+        __syncthreads();
+      }
+      // convergence check on T of dimension j1: warp b checks column b
+      {
+        const long long t0 = clk();
+        const int wp = tid >> 5, lane = tid & 31;
+        if (wp < B) {
+          const int b = wp;
+          double* d = reinterpret_cast<double*>(S.A) + (size_t)b * 4 * m;
+          double* e = d + m;
+          double* q0 = e + m;
+          double* qm = q0 + m;
+          for (int k = lane; k < j1; k += 32) {
+            d[k] = S.alpha[k * B + b];
+            e[k] = k + 1 < j1 ? S.beta[k * B + b] : 0.0;
+          }
+          __syncwarp();
+          bool ok = true;
+          if (lane == 0) ok = tridiag_eig_rows(j1, d, e, q0, qm);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          __syncwarp();
+          if (!ok && lane == 0) atomicOr(&S.ctl->status, 2);
+          const double bl = S.beta[(j1 - 1) * B + b];
+          const double s = select_step(j1, d, q0, qm, bl, s_rem, tol, zr, zi);
+          if (lane == 0) S.sb[b] = s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double s = S.sb[0];
+          for (int b = 1; b < B; ++b) s = fmin(s, S.sb[b]);
+          S.ctl->s_acc = s;
+        }
+        __syncthreads();
+        s_acc = S.ctl->s_acc;
+        cy[1] += clk() - t0;
+      }
+      if (S.ctl->status & 3) return;
+      if (j1 == m || s_acc >= s_rem) {
+        m_eff = j1;
+        break;
+      }
+      j0 = j1;
+      j1 = min(m, j1 + it.every);
+    }
+    s_acc = fmin(s_acc, s_rem);
+    if (!(s_acc > 1e-13 * s_rem) && !(s_acc >= s_rem)) {
+      if (tid == 0) S.ctl->status |= 4;
+      __syncthreads();
+      return;
+    }
+    const bool final_basis = s_acc >= s_rem || s_done + s_acc * (1.0 + 1e-13) >= 1.0;
+    // full eigendecomposition of the accepted basis and the combination coefficients
+    //   cc[k][b] = beta0_b sum_l Q_b[k][l] e^{s_acc z theta_l} Q_b[0][l]   (as k_tridiag_coef)
+    {
+      const long long t0 = clk();
+      const int wp = tid >> 5, lane = tid & 31;
+      const size_t fstride = (size_t)m * m + 4 * (size_t)m + 2;
+      for (int r0 = 0; r0 < B; r0 += a.L.ncol) {
+        const int b = r0 + wp;
+        if (wp < a.L.ncol && b < B) {
+          double* Qm = reinterpret_cast<double*>(S.A) + (size_t)wp * fstride;
+          double* d = Qm + (size_t)m * m;
+          double* e = d + m;
+          double* fg = e + m;     // 2 m doubles
+          double* rot = fg + 2 * m;
+          for (int k = lane; k < m_eff; k += 32) {
+            d[k] = S.alpha[k * B + b];
+            e[k] = k + 1 < m_eff ? S.beta[k * B + b] : 0.0;
+          }
+          __syncwarp();
+          const bool ok = tridiag_eig_warp(m_eff, d, e, Qm, rot);
+          if (!ok && lane == 0) atomicOr(&S.ctl->status, 2);
+          for (int l = lane; l < m_eff; l += 32) {
+            const double2 f = cexp_scaled(s_acc, zr, zi, d[l]);
+            const double g = Qm[l];  // row 0
+            fg[2 * l] = f.x * g;
+            fg[2 * l + 1] = f.y * g;
+          }
+          __syncwarp();
+          const double b0 = S.beta0[b];
+          for (int k = lane; k < m_eff; k += 32) {
+            double re = 0.0, im = 0.0;
+            for (int l = 0; l < m_eff; ++l) {
+              const double q = Qm[(size_t)k * m_eff + l];
+              re = fma(q, fg[2 * l], re);
+              im = fma(q, fg[2 * l + 1], im);
+            }
+            S.cc[k * B + b] = make_double2(b0 * re, b0 * im);
+          }
+        }
+        __syncthreads();
+      }
+      cy[2] += clk() - t0;
+    }
+    if (S.ctl->status & 3) return;
+    for (int e = tid; e < m_eff * B; e += kPNT) {
+      const double2 ck = S.cc[e];
+      const double f = S.sc[e];
+      S.fc[3 * B + e] = make_float2((float)(ck.x * f), (float)(ck.y * f));
+    }
+    __syncthreads();
+    // out = sum_{k < m_eff} cc_k sc_k u_k (in place when out aliases the current state: each
+    // element is read and then written by the same thread)
+    for (int r = tid; r < D; r += kPNT) {
+#pragma unroll
+      for (int q = 0; q < npairs(B); ++q) {
+        const int c0 = B >= 2 ? 2 * q : 0, c1 = B >= 2 ? 2 * q + 1 : 0;
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        for (int k = 0; k < m_eff; ++k) {
+          float2 v0, v1;
+          ld_pair<B>(U(k) + (size_t)r * B, q, v0, v1);
+          const float2 k0 = S.fc[(3 + k) * B + c0], k1 = S.fc[(3 + k) * B + c1];
+          cmac(a0, k0.x, k0.y, v0);
+          cmac(a1, k1.x, k1.y, v1);
+        }
+        st_pair<B>(out + (size_t)r * B, q, a0, a1);
+      }
+    }
+    __syncthreads();
+    if (final_basis) {
+      s_rem = 0.0;
+    } else {
+      s_done += s_acc;
+      s_rem -= s_acc;
+      cur = out;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- the persistent kernel
+// Chain of syk_otoc with rho split into quarters (Eq. F_reg):
+//   ua = rho^{1/8} psi~, ub = rho^{1/4} chi_j ua; per time t_k: ua, ub advanced by U(t_k - t_{k-1}),
+//   pr = rho^{1/4} U(t_k)^dag chi_i ua, qs = rho^{1/4} U(t_k)^dag chi_i ub, F_k = <pr | chi_j qs>.
+template <int B, int RPT>
+__global__ void __launch_bounds__(kPNT, 1) k_otoc_items(const __grid_constant__ PArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  PSmem S(smem, a.L);
+  const int tid = threadIdx.x;
+  const size_t vmax = (size_t)a.vmax;
+  float2* base = a.ws + (size_t)blockIdx.x * (size_t)(a.m + 5) * vmax;
+  float2* basis = base;
+  float2* ua = base + (size_t)a.m * vmax;
+  float2* ub = ua + vmax;
+  float2* pr = ub + vmax;
+  float2* qs = pr + vmax;
+  float2* tmp = qs + vmax;
+  for (;;) {
+    if (tid == 0) {
+      S.ctl->item = atomicAdd(a.next, 1);
+      S.ctl->status = 0;
+    }
+    __syncthreads();
+    const int q = S.ctl->item;
+    if (q >= a.nitems) break;
+    const PItem it = a.items[q];
+    const long long t_all = clk();
+    long long cy[3] = {0, 0, 0}, mv = 0, nb = 0;
+    const double be = it.beta;
+    const int n = it.n, D = it.D;
+    bool failed = false;
+    auto bad = [&]() -> bool { return (S.ctl->status) != 0; };
+    cta_expmv<B, RPT>(a, it, 0, -be / 8.0, 0.0, it.psi0, ua, basis, S, cy, mv, nb);
+    failed = bad();
+    if (!failed) {
+      cta_chi<B>(n, D, a.j, 1, ua, tmp);
+      cta_expmv<B, RPT>(a, it, 1, -be / 4.0, 0.0, tmp, ub, basis, S, cy, mv, nb);
+      failed = bad();
+    }
+    double tcur = 0.0;
+    for (int k = 0; k < a.nt && !failed; ++k) {
+      const double tk = a.t[k], dt = tk - tcur;
+      if (dt > 0.0) {
+        cta_expmv<B, RPT>(a, it, 0, 0.0, -dt, ua, ua, basis, S, cy, mv, nb);
+        if ((failed = bad())) break;
+        cta_expmv<B, RPT>(a, it, 1, 0.0, -dt, ub, ub, basis, S, cy, mv, nb);
+        if ((failed = bad())) break;
+        tcur = tk;
+      }
+      cta_chi<B>(n, D, a.i, 1, ua, pr);  // p (odd)
+      cta_chi<B>(n, D, a.i, 0, ub, qs);  // q (even)
+      cta_expmv<B, RPT>(a, it, 1, -be / 4.0, tk, pr, pr, basis, S, cy, mv, nb);
+      if ((failed = bad())) break;
+      cta_expmv<B, RPT>(a, it, 0, -be / 4.0, tk, qs, qs, basis, S, cy, mv, nb);
+      if ((failed = bad())) break;
+      cta_chi<B>(n, D, a.j, 1, qs, tmp);  // chi_j s (odd)
+      cta_dot<B>(pr, tmp, D, S, S.h);
+      if (tid < B) it.F[(size_t)k * B + tid] = S.h[tid];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      long long* st = a.stat + (size_t)q * kStWords;
+      st[kStStatus] = S.ctl->status;
+      st[kStMatvecs] = mv;
+      st[kStBases] = nb;
+      st[kStCyMatvec] = cy[0];
+      st[kStCyCheck] = cy[1];
+      st[kStCyEig] = cy[2];
+      st[kStCyAll] = clk() - t_all;
+    }
+    __syncthreads();  // ctl is rewritten by the next item
+  }
+}
+
+using KFn = void (*)(PArgs);
+KFn kernel_for(int B) {
+  switch (B) {
+    case 1: return k_otoc_items<1, 4>;
+    case 2: return k_otoc_items<2, 4>;
+    case 4: return k_otoc_items<4, 2>;
+    case 8: return k_otoc_items<8, 2>;
+    case 16: return k_otoc_items<16, 1>;
+    default: return nullptr;
+  }
+}
+
+size_t a16(size_t v) { return (v + 15) & ~size_t(15); }
+
+// Shared-memory layout for items of at most vmax elements per vector, batch B, Krylov m;
+// returns false if it exceeds `limit` bytes.
+bool make_layout(long long vmax, int B, int m, int limit, PLayout* L) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += a16(bytes);
+    return (int)o;
+  };
+  const size_t vec = (size_t)vmax * sizeof(float2);
+  const size_t chk = (size_t)B * 4 * m * sizeof(double);
+  const size_t fcol = ((size_t)m * m + 4 * (size_t)m + 2) * sizeof(double);
+  // everything but region A
+  size_t rest = 0;
+  {
+    const size_t parts[] = {kPG * sizeof(uint4),           kPG * 32 * sizeof(float2),   (size_t)m * B * 8,
+                            (size_t)m * B * 8,              (size_t)(m + 1) * B * 8,     (size_t)B * 8,
+                            (size_t)B * 16,                 (size_t)B * 16,              (size_t)m * B * 16,
+                            (size_t)kPWarps * B * 16,       (size_t)B * 8,               (size_t)(m + 3) * B * 8,
+                            sizeof(PCtl)};
+    for (size_t p : parts) rest += a16(p);
+  }
+  int ncol = std::min(B, kPWarps);
+  const size_t a0 = std::max(vec, chk);
+  while (ncol > 1 && rest + a16(std::max(a0, ncol * fcol)) > (size_t)limit) --ncol;
+  const size_t A = a16(std::max(a0, ncol * fcol));
+  if (rest + A > (size_t)limit) return false;
+  L->A = take(A);
+  L->rec = take(kPG * sizeof(uint4));
+  L->tab = take(kPG * 32 * sizeof(float2));
+  L->alpha = take((size_t)m * B * 8);
+  L->beta = take((size_t)m * B * 8);
+  L->sc = take((size_t)(m + 1) * B * 8);
+  L->beta0 = take((size_t)B * 8);
+  L->h = take((size_t)B * 16);
+  L->n2 = take((size_t)B * 16);
+  L->cc = take((size_t)m * B * 16);
+  L->red = take((size_t)kPWarps * B * 16);
+  L->sb = take((size_t)B * 8);
+  L->fc = take((size_t)(m + 3) * B * 8);
+  L->ctl = take(sizeof(PCtl));
+  L->total = (int)off;
+  L->ncol = ncol;
+  return true;
+}
+
+std::atomic<int> g_persistent{1};
+std::mutex g_report_mtx;
+long long g_report[kBatchReportWords] = {};
+
+}  // namespace
+
+bool batch_persistent_enabled() { return g_persistent.load() != 0; }
+
+int smem_optin_limit() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+    return 48 * 1024;
+  return v;
+}
+
+bool batch_item_persistent_ok(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m) {
+  if (!batch_persistent_enabled() || dtype != SYK_C64 || lanczos_orth(SYK_C64) != kOrthLocal) return false;
+  if (!(B == 1 || B == 2 || B == 4 || B == 8 || B == 16) || t->n < 2) return false;
+  if (B >= 2 && (reinterpret_cast<uintptr_t>(psi0) & 15)) return false;
+  PLayout L;
+  return make_layout((long long)t->D * B, (int)B, m, smem_optin_limit(), &L);
+}
+
+// Runs the items (all with batch B, all eligible) as one persistent launch on stream st; fills
+// each item's host F_re_im and status.  Synchronises st.
+int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& idx, int64_t B, int i, int j,
+                          const double* t, int nt, int m, double tol, int* item_status, cudaStream_t st,
+                          long long* report) {
+  const int ni = (int)idx.size();
+  if (ni == 0) return SYK_OK;
+  KFn fn = kernel_for((int)B);
+  if (!fn) {
+    set_error("persistent batch: unsupported batch %lld", (long long)B);
+    return SYK_EINVAL;
+  }
+  // largest sectors first, so that the long items do not form the tail
+  std::vector<int> order(idx);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return items[x].terms->D > items[y].terms->D; });
+  long long vmax = 0;
+  for (int k : order) vmax = std::max<long long>(vmax, (long long)items[k].terms->D * B);
+  PLayout L;
+  if (!make_layout(vmax, (int)B, m, smem_optin_limit(), &L)) {
+    set_error("persistent batch: items do not fit in shared memory");
+    return SYK_EINVAL;
+  }
+  const int grid = std::min(ni, sm_count());
+  Scratch sc(st);
+  void *d_items, *d_stat, *d_next, *d_t, *d_F, *d_ws;
+  SYK_TRY(sc.alloc(&d_items, sizeof(PItem) * ni));
+  SYK_TRY(sc.alloc(&d_stat, sizeof(long long) * kStWords * ni));
+  SYK_TRY(sc.alloc(&d_next, sizeof(int)));
+  SYK_TRY(sc.alloc(&d_t, sizeof(double) * nt));
+  SYK_TRY(sc.alloc(&d_F, sizeof(double2) * (size_t)nt * B * ni));
+  SYK_TRY(sc.alloc(&d_ws, sizeof(float2) * (size_t)vmax * (m + 5) * grid));
+  std::vector<PItem> h(ni);
+  for (int q = 0; q < ni; ++q) {
+    const syk_otoc_item& itm = items[order[q]];
+    const syk_terms* T = itm.terms;
+    ApplyParams P;
+    SYK_TRY(make_apply_params(T, 0, SYK_C64, &P));
+    const void* psi = nullptr;
+    SYK_TRY(device_input(itm.psi0, sizeof(float2) * (size_t)T->D * B, sc, &psi));
+    PItem& p = h[q];
+    p.m4_rec = P.m4_rec;
+    p.m4_t32 = static_cast<const float2*>(P.m4_tab);
+    p.m2_rec = P.m2_rec;
+    p.m2_t32 = static_cast<const float2*>(P.m2_tab);
+    p.wd32 = static_cast<const float*>(P.wd);
+    p.psi0 = static_cast<const float2*>(psi);
+    p.F = static_cast<double2*>(d_F) + (size_t)q * nt * B;
+    p.beta = itm.beta;
+    p.rho = T->rho_est;
+    p.n = T->n;
+    p.D = (int)T->D;
+    p.n4 = T->n4;
+    p.n2 = T->n2;
+    // checks every ~(check cost / matvec cost) vectors: a check (FP64 eigensolve) ~0.3 ms,
+    // a matvec on one SM ~8 nnz B flop at 2e11 flop/s
+    const double mv_ms = 8.0 * double(T->D) * double(T->n4 + T->n2 + 1) * double(B) / 2.0e8;
+    p.every = std::max(2, std::min(8, (int)std::lround(0.3 / std::max(mv_ms, 1e-6))));
+    p.pad = 0;
+  }
+  SYK_CUDA_CHECK(cudaMemcpyAsync(d_items, h.data(), sizeof(PItem) * ni, cudaMemcpyHostToDevice, st));
+  SYK_CUDA_CHECK(cudaMemcpyAsync(d_t, t, sizeof(double) * nt, cudaMemcpyHostToDevice, st));
+  PArgs a;
+  a.items = static_cast<const PItem*>(d_items);
+  a.nitems = ni;
+  a.next = static_cast<int*>(d_next);
+  a.stat = static_cast<long long*>(d_stat);
+  a.t = static_cast<const double*>(d_t);
+  a.nt = nt;
+  a.i = i;
+  a.j = j;
+  a.m = m;
+  a.tol = tol;
+  a.bt = 64.0 * 5.96e-8;
+  a.ws = static_cast<float2*>(d_ws);
+  a.vmax = vmax;
+  a.L = L;
+  SYK_TRY(ensure_smem_limit(reinterpret_cast<const void*>(fn), L.total));
+  // the queue reset and the persistent launch, as one CUDA graph
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  SYK_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(d_next, 0, sizeof(int), st);
+  fn<<<grid, kPNT, L.total, st>>>(a);
+  const cudaError_t el = cudaGetLastError();
+  const cudaError_t ec = cudaStreamEndCapture(st, &g);
+  if (el != cudaSuccess || ec != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    set_error("persistent batch: capture failed: %s", cudaGetErrorString(el != cudaSuccess ? el : ec));
+    return SYK_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    set_error("persistent batch: graph instantiation failed: %s", cudaGetErrorString(ei));
+    return SYK_ECUDA;
+  }
+  const cudaError_t eg = cudaGraphLaunch(ge, st);
+  count_launch(1);
+  std::vector<long long> hst((size_t)kStWords * ni);
+  std::vector<double2> hF((size_t)nt * B * ni);
+  cudaError_t e1 = eg;
+  if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(hst.data(), d_stat, sizeof(long long) * hst.size(), cudaMemcpyDeviceToHost, st);
+  if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(hF.data(), d_F, sizeof(double2) * hF.size(), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(ge);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    set_error("persistent batch: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    return SYK_ECUDA;
+  }
+  int rc = SYK_OK;
+  long long mv_states = 0, bases = 0, cym = 0, cyc = 0, cye = 0, cya = 0;
+  for (int q = 0; q < ni; ++q) {
+    const int k = order[q];
+    const long long* s = &hst[(size_t)q * kStWords];
+    const int bits = (int)s[kStStatus];
+    int irc = SYK_OK;
+    if (bits) {
+      irc = SYK_ENUMERIC;
+      if (rc == SYK_OK) {
+        set_error("persistent batch: item %d: %s", k,
+                  (bits & 1) ? "non-finite Lanczos scalar"
+                             : (bits & 2) ? "tridiagonal eigensolver did not converge"
+                                          : "Krylov step collapsed or too many bases; raise krylov_dim or tol");
+        rc = irc;
+      }
+    }
+    if (item_status) item_status[k] = irc;
+    double* F = items[k].F_re_im;
+    for (size_t e = 0; e < (size_t)nt * B; ++e) {
+      F[2 * e] = hF[(size_t)q * nt * B + e].x;
+      F[2 * e + 1] = hF[(size_t)q * nt * B + e].y;
+    }
+    mv_states += s[kStMatvecs] * B;
+    bases += s[kStBases];
+    cym += s[kStCyMatvec];
+    cyc += s[kStCyCheck];
+    cye += s[kStCyEig];
+    cya += s[kStCyAll];
+  }
+  count_applies(mv_states);
+  count_bases(bases);
+  if (report) {
+    report[0] += ni;
+    report[2] += grid;
+    report[3] += cym;
+    report[4] += cyc;
+    report[5] += cye;
+    report[6] += cya;
+    report[7] += mv_states;
+  }
+  return rc;
+}
+
+void batch_report_store(const long long* r) {
+  std::lock_guard<std::mutex> lk(g_report_mtx);
+  for (int k = 0; k < kBatchReportWords; ++k) g_report[k] = r[k];
+}
+
+void batch_report_load(long long* r) {
+  std::lock_guard<std::mutex> lk(g_report_mtx);
+  for (int k = 0; k < kBatchReportWords; ++k) r[k] = g_report[k];
+}
+
+}  // namespace syk
+
+extern "C" int syk_batch_persistent(int on) {
+  if (on != 0 && on != 1) {
+    syk::set_error("syk_batch_persistent: mode must be 0 or 1 (got %d)", on);
+    return SYK_EINVAL;
+  }
+  return syk::g_persistent.exchange(on);
+}
+
+extern "C" int syk_batch_report(long long* out, int n) {
+  if (!out || n < 1) {
+    syk::set_error("syk_batch_report: need an output array");
+    return SYK_EINVAL;
+  }
+  long long r[syk::kBatchReportWords];
+  syk::batch_report_load(r);
+  for (int k = 0; k < n && k < syk::kBatchReportWords; ++k) out[k] = r[k];
+  return SYK_OK;
+}

@@ -280,10 +280,12 @@ extern "C" int syk_correlator_G_imag(const syk_terms* terms, double beta, int i,
 }
 
 // ---------------------------------------------------------------- batched workload
-// Independent work items (coupling draws of any N, with their beta and states) are taken,
-// largest first, from a shared counter by `nworkers` host threads, each driving its own non-blocking CUDA
-// stream, so items of small sectors run concurrently and fill the GPU together.  Each
-// distinct (N, dtype, batch) is autotuned first on the calling thread.
+// Items whose whole chain fits one CTA run as one persistent launch (syk_batch.cu), driven by
+// one host thread on its own stream.  The other independent work items (coupling draws of any
+// N, with their beta and states) are taken, largest first, from a shared counter by `nworkers`
+// host threads, each driving its own non-blocking CUDA stream, so items of small sectors run
+// concurrently and fill the GPU together.  Each distinct (N, dtype, batch) of those is
+// autotuned first on the calling thread.
 extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const double* t, int nt,
                               int dtype, int krylov_dim, double tol, int nworkers, int* item_status) {
   syk::NvtxRange nvtx_range_("syk_otoc_batch");
@@ -302,10 +304,22 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
   }
   int dev = 0;
   SYK_CUDA_CHECK(cudaGetDevice(&dev));
+  // items for the persistent launch, by batch size (1, 2, 4, 8, 16); the rest go to the workers
+  std::vector<char> persistent(nitems, 0);
+  std::vector<std::vector<int>> pgroups(5);
+  for (int k = 0; k < nitems; ++k)
+    if (batch_item_persistent_ok(items[k].terms, items[k].nstates, items[k].psi0, dtype, krylov_dim)) {
+      persistent[k] = 1;
+      int g = 0;
+      while ((int64_t(1) << g) < items[k].nstates) ++g;
+      pgroups[g].push_back(k);
+    }
+  long long report[kBatchReportWords] = {};
   // tune the matvec shape of every distinct (N, batch) once
   {
     std::vector<std::pair<int, int64_t>> done;
     for (int k = 0; k < nitems; ++k) {
+      if (persistent[k]) continue;
       const auto key = std::make_pair(items[k].terms->N, items[k].nstates);
       if (std::find(done.begin(), done.end(), key) != done.end()) continue;
       done.push_back(key);
@@ -315,8 +329,11 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
     }
   }
   // largest items first (state size x states), so the long ones do not form the tail
-  std::vector<int> order(nitems);
-  for (int k = 0; k < nitems; ++k) order[k] = k;
+  std::vector<int> order;
+  for (int k = 0; k < nitems; ++k)
+    if (!persistent[k]) order.push_back(k);
+  const int nrest = (int)order.size();
+  report[1] = nrest;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return double(items[a].terms->D) * items[a].nstates > double(items[b].terms->D) * items[b].nstates;
   });
@@ -324,6 +341,43 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
   std::mutex err_mtx;
   int first_rc = SYK_OK;
   std::string first_msg;
+  // the persistent launch(es), one per batch size, on their own stream and host thread
+  auto persistent_driver = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t st = nullptr;
+    int rc = SYK_OK;
+    std::string msg;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = SYK_ECUDA;
+      msg = "cannot create a stream";
+    }
+    // statuses start at a positive "not run" mark; a launch that returns them overwrites it
+    if (item_status)
+      for (int g = 0; g < 5; ++g)
+        for (int k : pgroups[g]) item_status[k] = 1;
+    for (int g = 0; g < 5 && rc == SYK_OK; ++g) {
+      if (pgroups[g].empty()) continue;
+      NvtxRange range("syk_otoc_batch persistent launch");
+      rc = otoc_batch_persistent(items, pgroups[g], int64_t(1) << g, i, j, t, nt, krylov_dim, tol, item_status, st,
+                                 report);
+      if (rc != SYK_OK) msg = syk_last_error();
+    }
+    if (rc != SYK_OK && item_status)
+      for (int g = 0; g < 5; ++g)
+        for (int k : pgroups[g])
+          if (item_status[k] == 1) item_status[k] = rc;
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    if (rc != SYK_OK) {
+      std::lock_guard<std::mutex> lk(err_mtx);
+      if (first_rc == SYK_OK) {
+        first_rc = rc;
+        first_msg = "persistent launch: " + msg;
+      }
+    }
+  };
   auto worker = [&]() {
     cudaSetDevice(dev);
     cudaStream_t st = nullptr;
@@ -335,7 +389,7 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
       }
       return;
     }
-    for (int q = next++; q < nitems; q = next++) {
+    for (int q = next++; q < nrest; q = next++) {
       const int k = order[q];
       const syk_otoc_item& it = items[k];
       NvtxRange item_range("syk_otoc_batch item");
@@ -355,9 +409,12 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
     cudaStreamDestroy(st);
   };
   std::vector<std::thread> pool;
-  const int nw = std::min(nworkers, nitems);
+  const bool any_persistent = nrest < nitems;
+  if (any_persistent) pool.emplace_back(persistent_driver);
+  const int nw = std::min(nworkers, nrest);
   for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
   for (auto& th : pool) th.join();
+  batch_report_store(report);
   if (first_rc != SYK_OK) set_error("syk_otoc_batch: %s", first_msg.c_str());
   return first_rc;
 }

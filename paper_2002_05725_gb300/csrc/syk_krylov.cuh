@@ -111,6 +111,21 @@ void* pinned_scratch(size_t bytes);
 int lanczos_begin(int dtype, const void* psi, KrylovWS& ws, cudaStream_t st);
 int lanczos_steps(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st);
 
+// Persistent batched OTOC (syk_batch.cu).  batch_item_persistent_ok: the item can run in the
+// persistent kernel (complex64 with the three-term recurrence, a batch of 1, 2, 4, 8 or 16
+// states, its sector vector and the launch's scalars within one CTA's shared memory).
+// otoc_batch_persistent runs such items of one batch size as ONE launch on stream st and
+// fills their host results and statuses (synchronises st); report gets, added: items, -,
+// CTAs, clock cycles in matvecs, convergence checks, full eigendecompositions, all item work,
+// and H applications (states x matvecs).
+constexpr int kBatchReportWords = 8;
+bool batch_persistent_enabled();
+bool batch_item_persistent_ok(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m);
+int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& idx, int64_t B, int i, int j,
+                          const double* t, int nt, int m, double tol, int* item_status, cudaStream_t st,
+                          long long* report);
+void batch_report_store(const long long* r);
+
 // Device buffers owned by one library call (freed, stream-ordered, when it returns).
 struct Scratch {
   cudaStream_t st;

@@ -79,6 +79,8 @@ def load(build_if_missing: bool = False):
         "syk_c128_arith": (i32, [i32]),
         "syk_status": (i32, [vp, i32, vp]),
         "syk_lanczos_orth": (i32, [i32, i32]),
+        "syk_batch_persistent": (i32, [i32]),
+        "syk_batch_report": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -96,7 +98,8 @@ def exported_symbols():
             "syk_autotune_apply", "syk_autotune_export", "syk_autotune_import", "syk_otoc_grad",
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
             "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak",
-            "syk_matvec_launches", "syk_c128_arith", "syk_status", "syk_lanczos_orth"]
+            "syk_matvec_launches", "syk_c128_arith", "syk_status", "syk_lanczos_orth", "syk_batch_persistent",
+            "syk_batch_report"]
 
 
 def _check(rc: int, what: str):
@@ -373,6 +376,26 @@ def syk_otoc_batch(items, i: int, j: int, times, dtype: int = SYK_C64, krylov_di
                                  status.ctypes.data), "syk_otoc_batch")
     del keep
     return [F[..., 0] + 1j * F[..., 1] for F in outs]
+
+
+def syk_batch_persistent(on: bool = True) -> bool:
+    """Whether syk_otoc_batch runs the items that fit one CTA in its persistent launch; returns
+    the previous setting."""
+    rc = load().syk_batch_persistent(int(bool(on)))
+    if rc < 0:
+        _check(rc, "syk_batch_persistent")
+    return bool(rc)
+
+
+BATCH_REPORT_KEYS = ("persistent_items", "stream_items", "persistent_ctas", "cycles_matvec", "cycles_check",
+                     "cycles_eig", "cycles_items", "h_applies")
+
+
+def syk_batch_report() -> dict:
+    """Counters of the last syk_otoc_batch call (see include/syk.h)."""
+    out = np.zeros(len(BATCH_REPORT_KEYS), dtype=np.int64)
+    _check(load().syk_batch_report(out.ctypes.data, len(out)), "syk_batch_report")
+    return {k: int(v) for k, v in zip(BATCH_REPORT_KEYS, out)}
 
 
 def syk_lowest_eigenvalues(terms: Terms, k: int, psi0, parity: int = 0, max_steps: int = 1024, tol: float = 1e-8,

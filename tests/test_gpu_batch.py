@@ -29,7 +29,9 @@ def test_otoc_batch_mixed_N(dt):
         refs.append((single, N, J, beta, psi))
     out = syk.syk_otoc_batch(items, 0, 1, ts, dtype=code, krylov_dim=30, tol=tol, nworkers=3)
     for F, (single, N, J, beta, psi) in zip(out, refs):
-        assert rel(F, single) < (1e-12 if dt == "c128" else 1e-6)
+        # complex64 items run in the persistent launch, whose convergence checks follow their own
+        # plan: the two evaluations agree to a few tol = 1e-7 Krylov steps
+        assert rel(F, single) < (1e-12 if dt == "c128" else 5e-6)
         # every item against the exact oracle, the N = 20 and 24 items (tiled and coset
         # matvecs) included
         Fr = co.F_state(evolve.SectorSystem(N, J), beta, 0, 1, ts, psi.T)
