@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--batched-Ns", default="20,24,28,32,36,40", help="sizes of the --batched workload")
     ap.add_argument("--graphs", default="segments", choices=["off", "segments", "device"],
                     help="launch mode of the Krylov evolutions of the --batched workload (syk_use_graphs 0/1/2)")
-    ap.add_argument("--persistent", default="on", choices=["on", "off"],
+    ap.add_argument("--persistent", default="on", choices=["on", "off", "split"],
                     help="run the --batched items that fit one CTA in the persistent launch (on) or every item on "
                          "the per-item streams (off)")
     ap.add_argument("--grad", action="store_true",
@@ -525,7 +525,7 @@ def run_batched(a, rank, world, local_rank, draws):
     times = time_grid(a.npts, a.tmax)
     Ns, betas = [int(v) for v in a.batched_Ns.split(",")], [1.0, 3.0, 10.0]
     syk.syk_use_graphs({"off": 0, "segments": 1, "device": 2}[a.graphs])
-    prev_persistent = syk.syk_batch_persistent(a.persistent == "on")
+    prev_persistent = syk.syk_batch_persistent({"off": 0, "on": 1, "split": 2}[a.persistent])
     items = []
     for d in range(draws):
         for N in Ns:
@@ -552,8 +552,14 @@ def run_batched(a, rank, world, local_rank, draws):
     syk.syk_batch_persistent(prev_persistent)
     curves = 8 * len(items)
     cyc = max(rep["cycles_items"], 1)
+    hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
     persistent = {"items": rep["persistent_items"], "per_item_path_items": rep["stream_items"],
-                  "ctas": rep["persistent_ctas"], "h_applies": rep["h_applies"],
+                  "subitems": rep["persistent_subitems"], "ctas": rep["persistent_ctas"],
+                  "h_applies": rep["h_applies"], "convergence_checks": rep["checks"],
+                  "full_eigendecompositions": rep["full_eigs"],
+                  "seconds_per_subitem": rep["cycles_items"] / hz / max(rep["persistent_subitems"], 1),
+                  "ms_per_check": rep["cycles_check"] / hz * 1e3 / max(rep["checks"], 1),
+                  "ms_per_full_eig": rep["cycles_eig"] / hz * 1e3 / max(rep["full_eigs"], 1),
                   "cycle_shares": {"matvec": rep["cycles_matvec"] / cyc, "convergence_checks": rep["cycles_check"] / cyc,
                                    "full_eigendecompositions": rep["cycles_eig"] / cyc},
                   "note": "items whose sector vector fits one CTA's shared memory run as one persistent launch "

@@ -232,12 +232,15 @@ int syk_correlator_G_imag(const syk_terms* terms, double beta, int i, const doub
 /* syk_otoc_batch -- the batched workload: many independent OTOC evaluations
  * (coupling draws of any N, each with its beta and its D x nstates random
  * states, device or host memory) at the common times t, Majoranas i, j, dtype
- * and Krylov settings.  Items whose whole chain fits one CTA (complex64 with
- * the three-term Lanczos recurrence, nstates in {1, 2, 4, 8, 16}, the sector
- * vector of D x nstates values within shared memory: N <= 24 at 8 states)
- * run as ONE persistent kernel launch (a CUDA graph of the queue reset and
- * the kernel): each CTA takes items from a device-side queue and evaluates an
- * item's entire chain -- Lanczos evolutions with FP64 scalars, tridiagonal
+ * and Krylov settings.  complex64 items (three-term Lanczos recurrence) run
+ * as ONE persistent kernel launch (a CUDA graph of the queue reset and the
+ * kernel) when their states split into sub-items of Bs in {16, 8, 4, 2}
+ * states (or one state for one-state items), Bs a divisor of nstates, whose
+ * sector vectors of D x Bs values fit one CTA's shared memory (N <= 24 at 8
+ * states per CTA, N = 28 at 2, N = 30 for one-state items; items split over
+ * several CTAs only when the batch's split sub-items fill at least half the
+ * SMs): each CTA takes sub-items from a device-side queue and evaluates their
+ * entire chain -- Lanczos evolutions with FP64 scalars, tridiagonal
  * eigendecompositions, step control, Majoranas, dots -- with no host round
  * trip (syk_batch_persistent(0) turns this off).  The other items are taken,
  * largest first, by `nworkers` host threads, each with its own CUDA stream,
@@ -256,16 +259,19 @@ typedef struct {
 int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const double* t, int nt,
                    int dtype, int krylov_dim, double tol, int nworkers, int* item_status);
 /* syk_batch_persistent -- 1 (default): syk_otoc_batch runs the items that fit
- * one CTA in its persistent launch; 0: every item takes the per-item path.
- * Returns the previous mode.  Plumbing; no counterpart in the paper. */
+ * its persistent launch there (items split over several CTAs only when there
+ * are enough of them, see syk_otoc_batch); 2: split items always go there too;
+ * 0: every item takes the per-item path.  Returns the previous mode.
+ * Plumbing; no counterpart in the paper. */
 int syk_batch_persistent(int on);
 /* syk_batch_report -- counters of the last syk_otoc_batch call (host array of
- * n <= 8 words): items in the persistent launch, items on the per-item path,
- * CTAs of the persistent launch, and, summed over its items, SM clock cycles
- * spent in matvecs, in convergence checks (tridiagonal eigenvalues and step
- * selection), in the full eigendecompositions of accepted bases and in whole
- * items, and H applications (states x matvecs).  Measurement; no counterpart in
- * the paper. */
+ * n <= 11 words): items in the persistent launch, items on the per-item path,
+ * CTAs of the persistent launch; summed over its sub-items (one CTA's share of
+ * an item's states): SM clock cycles spent in matvecs, in convergence checks
+ * (tridiagonal eigenvalues and step selection), in the full
+ * eigendecompositions of accepted bases and in whole sub-items; H applications
+ * (states x matvecs), convergence checks, full eigendecompositions; and the
+ * number of sub-items.  Measurement; no counterpart in the paper. */
 int syk_batch_report(long long* out, int n);
 
 /* --------------------------------------------------------------- gradients

@@ -41,16 +41,23 @@ struct PItem {
   const float2* m2_t32;
   const float* wd32;
   const float2* psi0;  // D x B (device)
-  double2* F;          // nt x B results (device)
+  double2* F;          // F[k * Fld + c]: result of state c at time k (device)
   double beta, rho;
   int n, D, n4, n2;
   int every;           // Lanczos vectors between two convergence checks after the first
-  int pad;
+  int first8;          // the first check comes at first8/8 of the predicted Krylov dimension
+  int Fld;             // row stride of F (the parent item's state count)
 };
 
 // Per-item record written by the kernel.
 enum { kStStatus = 0, kStMatvecs = 1, kStBases = 2, kStCyMatvec = 3, kStCyCheck = 4, kStCyEig = 5, kStCyAll = 6,
-       kStWords = 8 };
+       kStChecks = 7, kStEigs = 8, kStWords = 10 };
+
+// Work and clock counters of one item.
+struct PCount {
+  long long cy[3];  // clock cycles: matvecs, convergence checks, full eigendecompositions
+  long long mv, nb, nck, neig;
+};
 
 // Shared-memory layout of a launch (byte offsets, computed on the host).
 struct PLayout {
@@ -70,8 +77,8 @@ struct PArgs {
   int nt, i, j;       // Majoranas i (W), j (V)
   int m;              // Krylov dimension
   double tol, bt;     // step tolerance, breakdown threshold of beta_j
-  float2* ws;         // per CTA: (m + 5) vectors of vmax elements
-  long long vmax;
+  float2* ws;         // per CTA: (m + 5) vectors of vmax elements, then cmax float2 of coefficients
+  long long vmax, cmax;
   PLayout L;
 };
 
@@ -244,15 +251,41 @@ __device__ __noinline__ void cta_chi(int n, int D, int maj, int sector_out, cons
 }
 
 // ---------------------------------------------------------------- matvec
+// The diagonal and popcount-2 coefficients of a row depend only on the row and the sector, so
+// they are evaluated once per item (each is an O(n) sum over the spins) and stored in the
+// CTA's workspace: dg[s * D + x] = c_0(x) and pc[(s * n2 + k) * D + x] = c_{m_k}(x) for the
+// popcount-2 masks m_k, sector s.
+__device__ __noinline__ void cta_coef(const PItem& it, float* dg, float2* pc) {
+  const int n = it.n, D = it.D;
+  for (int s = 0; s < 2; ++s)
+    for (int r = threadIdx.x; r < D; r += kPNT) {
+      const uint32_t xc = (uint32_t)r;
+      const uint32_t xf = xc | ((uint32_t)((__popc(xc) + s) & 1) << (n - 1));
+      dg[(size_t)s * D + r] = diag_coef<float>(it.wd32, n, xf);
+      for (int k = 0; k < it.n2; ++k) {
+        float cr, ci;
+        pc2_coef<float2, float>(it.m2_t32, k, n, __ldg(&it.m2_rec[k]), xf, cr, ci);
+        pc[((size_t)s * it.n2 + k) * D + r] = make_float2(cr, ci);
+      }
+    }
+  __syncthreads();
+}
+
 // y = H xs in sector `sector` (Supp. Sec. I.B; the sums of k_apply_rows), xs staged in shared
-// memory (D x B).  A thread owns RPT rows r0 + tid + i kPNT of each pass and all B columns;
-// rows wider than 16 bytes are read in 16-byte chunks in a lane-rotated order (chunk
-// (q + lane) mod Q into accumulator q) so that the 32 lanes of a warp hit distinct banks.  The
-// popcount-4 records and tables are staged in chunks of kPG masks.
+// memory (D x B).  A thread owns RPT rows r0 + tid + i kPNT of each pass (they differ in the
+// compact bits 9 and 10 only) and all B columns; rows wider than 16 bytes are read in 16-byte
+// chunks in a lane-rotated order (chunk (q + lane) mod Q into accumulator q) so that the 32
+// lanes of a warp hit distinct banks.  Popcount-4 records and tables are staged in chunks of
+// kPG masks; a mask's table index for rows 1 .. RPT-1 is row 0's XOR the record's row-flip
+// patterns of compact bits 9 and 10 (one extraction of the support bits per mask).
+// dg, pc: this sector's precomputed diagonal and popcount-2 coefficients (cta_coef).
 template <int B, int RPT>
-__device__ __noinline__ void cta_matvec(const PItem& it, int sector, const float2* __restrict__ xs, float2* __restrict__ y,
-                           PSmem& S) {
+__device__ __noinline__ void cta_matvec(const PItem& it, int sector, const float2* __restrict__ xs,
+                                        float2* __restrict__ y, PSmem& S, const float* __restrict__ dg,
+                                        const float2* __restrict__ pc) {
+  static_assert(RPT == 1 || RPT == 2 || RPT == 4, "row slots are the compact bits 9 and 10");
   constexpr int Q = B >= 2 ? B / 2 : 1;
+  constexpr int fsh = flip_shift(9);
   using V = typename std::conditional<(B >= 2), float4, float2>::type;
   const int tid = threadIdx.x;
   const int rot = (tid & 31) & (Q - 1);
@@ -266,17 +299,17 @@ __device__ __noinline__ void cta_matvec(const PItem& it, int sector, const float
     }
   };
   for (int r0 = 0; r0 < D; r0 += kPNT * RPT) {
-    uint32_t xr[RPT], xf[RPT];
+    uint32_t xr[RPT];
     bool ok[RPT];
     V acc[RPT][Q];
+    const uint32_t xr0 = (uint32_t)(r0 + tid);
+    const uint32_t xf0 = xr0 | ((uint32_t)((__popc(xr0) + sector) & 1) << (n - 1));
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
-      const int r = r0 + tid + i * kPNT;
-      ok[i] = r < D;
-      xr[i] = (uint32_t)(ok[i] ? r : 0);
-      xf[i] = xr[i] | ((uint32_t)((__popc(xr[i]) + sector) & 1) << (n - 1));
+      xr[i] = xr0 + (uint32_t)(i * kPNT);
+      ok[i] = (int)xr[i] < D;
       if (!ok[i]) continue;
-      const float c0 = diag_coef<float>(it.wd32, n, xf[i]);
+      const float c0 = dg[xr[i]];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const V v = x4[xr[i] * Q + ((q + rot) & (Q - 1))];
@@ -284,12 +317,11 @@ __device__ __noinline__ void cta_matvec(const PItem& it, int sector, const float
         else acc[i][q] = make_float2(c0 * v.x, c0 * v.y);
       }
       for (int k = 0; k < it.n2; ++k) {
-        const uint4 rec = __ldg(&it.m2_rec[k]);
-        float cr, ci;
-        pc2_coef<float2, float>(it.m2_t32, k, n, rec, xf[i], cr, ci);
-        const uint32_t pr = xr[i] ^ rec.x;
+        const uint32_t mx = __ldg(&it.m2_rec[k].x);
+        const float2 cf = pc[(size_t)k * D + xr[i]];
+        const uint32_t pr = xr[i] ^ mx;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) mac(acc[i][q], cr, ci, x4[pr * Q + ((q + rot) & (Q - 1))]);
+        for (int q = 0; q < Q; ++q) mac(acc[i][q], cf.x, cf.y, x4[pr * Q + ((q + rot) & (Q - 1))]);
       }
     }
     for (int c0 = 0; c0 < it.n4; c0 += kPG) {
@@ -300,15 +332,21 @@ __device__ __noinline__ void cta_matvec(const PItem& it, int sector, const float
       float4* dst = reinterpret_cast<float4*>(S.tab);
       for (int e = tid; e < cnt * 16; e += kPNT) dst[e] = __ldg(&src[e]);
       __syncthreads();
+      if (!ok[0]) continue;  // rows 1 .. RPT-1 lie above row 0
       for (int k = 0; k < cnt; ++k) {
         const uint4 rec = S.rec[k];
         const float2* T = S.tab + k * 32;
+        const uint32_t idx0 = supp_bits(xf0, rec.z) | ((__popc(rec.y & xf0) & 1u) << 4);
+        const uint32_t fl = rec.w >> fsh;
+        const uint32_t pr0 = xr0 ^ rec.x;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           if (!ok[i]) continue;
-          const uint32_t idx = supp_bits(xf[i], rec.z) | ((__popc(rec.y & xf[i]) & 1u) << 4);
-          const float2 cf = T[idx];
-          const uint32_t pr = xr[i] ^ rec.x;
+          uint32_t f = 0u;
+          if (i & 1) f ^= fl;
+          if (i & 2) f ^= fl >> 5;
+          const float2 cf = T[idx0 ^ (f & 31u)];
+          const uint32_t pr = pr0 ^ (uint32_t)(i * kPNT);
 #pragma unroll
           for (int q = 0; q < Q; ++q) mac(acc[i][q], cf.x, cf.y, x4[pr * Q + ((q + rot) & (Q - 1))]);
         }
@@ -334,11 +372,12 @@ __device__ __forceinline__ long long clk() { return clock64(); }
 // dimension, later ones every it.every vectors; restarts from 4 vectors on), the largest step
 // per basis whose estimate is <= tol for every column, restarts from the end state.
 // basis: slots 1..m of the Krylov basis (slot k at basis + (k-1) vmax); slot 0 is `in` or the
-// restart state.  Error bits go to S.ctl->status (1 non-finite scalar, 2 eigensolver, 4 step
+// restart state.  dgs, pcs: the item's precomputed diagonal and popcount-2 coefficients.  Error bits go to S.ctl->status (1 non-finite scalar, 2 eigensolver, 4 step
 // collapse or too many bases).
 template <int B, int RPT>
 __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sector, double zr, double zi, const float2* in,
-                          float2* out, float2* basis, PSmem& S, long long* cy, long long& mv, long long& nb) {
+                          float2* out, float2* basis, PSmem& S, PCount& pc, const float* dgs,
+                          const float2* pcs) {
   const int D = it.D, m = a.m, tid = threadIdx.x;
   const double tol = a.tol;
   if (zr == 0.0 && zi == 0.0) {
@@ -353,7 +392,7 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
         k = kk;
         break;
       }
-    S.ctl->first = min(m, max(4, (3 * k) / 4));
+    S.ctl->first = min(m, max(4, (it.first8 * k) / 8));
   }
   __syncthreads();
   const int first = S.ctl->first;
@@ -362,12 +401,12 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
   float2* xs = reinterpret_cast<float2*>(S.A);
   int bases = 0;
   while (s_rem > 0.0) {
-    if (++bases > kMaxBasesPerEvolution || nb >= kMaxBasesPerItem) {
+    if (++bases > kMaxBasesPerEvolution || pc.nb >= kMaxBasesPerItem) {
       if (tid == 0) S.ctl->status |= 4;
       __syncthreads();
       return;
     }
-    ++nb;
+    ++pc.nb;
     auto U = [&](int k) -> const float2* { return k == 0 ? cur : basis + (size_t)(k - 1) * a.vmax; };
     // beta0 = ||cur||, sc_0 = 1/beta0
     {
@@ -415,9 +454,9 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
         }
         float2* w = basis + (size_t)j * a.vmax;  // slot j+1
         const long long t0 = clk();
-        cta_matvec<B, RPT>(it, sector, xs, w, S);
-        cy[0] += clk() - t0;
-        ++mv;
+        cta_matvec<B, RPT>(it, sector, xs, w, S, dgs + (size_t)sector * D, pcs + (size_t)sector * it.n2 * D);
+        pc.cy[0] += clk() - t0;
+        ++pc.mv;
         // h_j = <v_j, w>
         cta_dot<B>(xs, w, D, S, S.h);
         if (tid < B) {
@@ -506,7 +545,8 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
         }
         __syncthreads();
         s_acc = S.ctl->s_acc;
-        cy[1] += clk() - t0;
+        pc.cy[1] += clk() - t0;
+        ++pc.nck;
       }
       if (S.ctl->status & 3) return;
       if (j1 == m || s_acc >= s_rem) {
@@ -564,7 +604,8 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
         }
         __syncthreads();
       }
-      cy[2] += clk() - t0;
+      pc.cy[2] += clk() - t0;
+      ++pc.neig;
     }
     if (S.ctl->status & 3) return;
     for (int e = tid; e < m_eff * B; e += kPNT) {
@@ -611,13 +652,15 @@ __global__ void __launch_bounds__(kPNT, 1) k_otoc_items(const __grid_constant__ 
   PSmem S(smem, a.L);
   const int tid = threadIdx.x;
   const size_t vmax = (size_t)a.vmax;
-  float2* base = a.ws + (size_t)blockIdx.x * (size_t)(a.m + 5) * vmax;
+  float2* base = a.ws + (size_t)blockIdx.x * ((size_t)(a.m + 5) * vmax + (size_t)a.cmax);
   float2* basis = base;
   float2* ua = base + (size_t)a.m * vmax;
   float2* ub = ua + vmax;
   float2* pr = ub + vmax;
   float2* qs = pr + vmax;
   float2* tmp = qs + vmax;
+  float* dgs = reinterpret_cast<float*>(tmp + vmax);  // 2 D floats, then 2 n2 D float2 (cta_coef)
+  float2* pcs = nullptr;
   for (;;) {
     if (tid == 0) {
       S.ctl->item = atomicAdd(a.next, 1);
@@ -628,48 +671,52 @@ __global__ void __launch_bounds__(kPNT, 1) k_otoc_items(const __grid_constant__ 
     if (q >= a.nitems) break;
     const PItem it = a.items[q];
     const long long t_all = clk();
-    long long cy[3] = {0, 0, 0}, mv = 0, nb = 0;
+    PCount pc = {{0, 0, 0}, 0, 0, 0, 0};
+    pcs = tmp + vmax + (size_t)it.D;  // after the 2 D diagonal floats
+    cta_coef(it, dgs, pcs);
     const double be = it.beta;
     const int n = it.n, D = it.D;
     bool failed = false;
     auto bad = [&]() -> bool { return (S.ctl->status) != 0; };
-    cta_expmv<B, RPT>(a, it, 0, -be / 8.0, 0.0, it.psi0, ua, basis, S, cy, mv, nb);
+    cta_expmv<B, RPT>(a, it, 0, -be / 8.0, 0.0, it.psi0, ua, basis, S, pc, dgs, pcs);
     failed = bad();
     if (!failed) {
       cta_chi<B>(n, D, a.j, 1, ua, tmp);
-      cta_expmv<B, RPT>(a, it, 1, -be / 4.0, 0.0, tmp, ub, basis, S, cy, mv, nb);
+      cta_expmv<B, RPT>(a, it, 1, -be / 4.0, 0.0, tmp, ub, basis, S, pc, dgs, pcs);
       failed = bad();
     }
     double tcur = 0.0;
     for (int k = 0; k < a.nt && !failed; ++k) {
       const double tk = a.t[k], dt = tk - tcur;
       if (dt > 0.0) {
-        cta_expmv<B, RPT>(a, it, 0, 0.0, -dt, ua, ua, basis, S, cy, mv, nb);
+        cta_expmv<B, RPT>(a, it, 0, 0.0, -dt, ua, ua, basis, S, pc, dgs, pcs);
         if ((failed = bad())) break;
-        cta_expmv<B, RPT>(a, it, 1, 0.0, -dt, ub, ub, basis, S, cy, mv, nb);
+        cta_expmv<B, RPT>(a, it, 1, 0.0, -dt, ub, ub, basis, S, pc, dgs, pcs);
         if ((failed = bad())) break;
         tcur = tk;
       }
       cta_chi<B>(n, D, a.i, 1, ua, pr);  // p (odd)
       cta_chi<B>(n, D, a.i, 0, ub, qs);  // q (even)
-      cta_expmv<B, RPT>(a, it, 1, -be / 4.0, tk, pr, pr, basis, S, cy, mv, nb);
+      cta_expmv<B, RPT>(a, it, 1, -be / 4.0, tk, pr, pr, basis, S, pc, dgs, pcs);
       if ((failed = bad())) break;
-      cta_expmv<B, RPT>(a, it, 0, -be / 4.0, tk, qs, qs, basis, S, cy, mv, nb);
+      cta_expmv<B, RPT>(a, it, 0, -be / 4.0, tk, qs, qs, basis, S, pc, dgs, pcs);
       if ((failed = bad())) break;
       cta_chi<B>(n, D, a.j, 1, qs, tmp);  // chi_j s (odd)
       cta_dot<B>(pr, tmp, D, S, S.h);
-      if (tid < B) it.F[(size_t)k * B + tid] = S.h[tid];
+      if (tid < B) it.F[(size_t)k * it.Fld + tid] = S.h[tid];
       __syncthreads();
     }
     if (tid == 0) {
       long long* st = a.stat + (size_t)q * kStWords;
       st[kStStatus] = S.ctl->status;
-      st[kStMatvecs] = mv;
-      st[kStBases] = nb;
-      st[kStCyMatvec] = cy[0];
-      st[kStCyCheck] = cy[1];
-      st[kStCyEig] = cy[2];
+      st[kStMatvecs] = pc.mv;
+      st[kStBases] = pc.nb;
+      st[kStCyMatvec] = pc.cy[0];
+      st[kStCyCheck] = pc.cy[1];
+      st[kStCyEig] = pc.cy[2];
       st[kStCyAll] = clk() - t_all;
+      st[kStChecks] = pc.nck;
+      st[kStEigs] = pc.neig;
     }
     __syncthreads();  // ctl is rewritten by the next item
   }
@@ -742,6 +789,7 @@ long long g_report[kBatchReportWords] = {};
 }  // namespace
 
 bool batch_persistent_enabled() { return g_persistent.load() != 0; }
+bool batch_persistent_split_always() { return g_persistent.load() == 2; }
 
 int smem_optin_limit() {
   int dev = 0, v = 0;
@@ -751,53 +799,84 @@ int smem_optin_limit() {
   return v;
 }
 
-bool batch_item_persistent_ok(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m) {
-  if (!batch_persistent_enabled() || dtype != SYK_C64 || lanczos_orth(SYK_C64) != kOrthLocal) return false;
-  if (!(B == 1 || B == 2 || B == 4 || B == 8 || B == 16) || t->n < 2) return false;
-  if (B >= 2 && (reinterpret_cast<uintptr_t>(psi0) & 15)) return false;
-  PLayout L;
-  return make_layout((long long)t->D * B, (int)B, m, smem_optin_limit(), &L);
+int batch_item_persistent_states(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m) {
+  if (!batch_persistent_enabled() || dtype != SYK_C64 || lanczos_orth(SYK_C64) != kOrthLocal) return 0;
+  (void)psi0;  // every sub-item gets its own aligned device copy of its columns
+  if (B < 1 || t->n < 2) return 0;
+  const int limit = smem_optin_limit();
+  for (int bs = 16; bs >= 1; bs >>= 1) {
+    if (B % bs != 0 || (bs == 1 && B > 1)) continue;
+    PLayout L;
+    if (make_layout((long long)t->D * bs, bs, m, limit, &L)) return bs;
+  }
+  return 0;
 }
 
-// Runs the items (all with batch B, all eligible) as one persistent launch on stream st; fills
-// each item's host F_re_im and status.  Synchronises st.
-int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& idx, int64_t B, int i, int j,
+// Runs the items of idx, each split into sub-items of Bs states (columns b0 .. b0 + Bs - 1 of
+// its D x nstates input, copied into an aligned device buffer of their own), as one
+// persistent launch on stream st; fills each item's host F_re_im and status.  Synchronises st.
+int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& idx, int64_t Bs, int i, int j,
                           const double* t, int nt, int m, double tol, int* item_status, cudaStream_t st,
                           long long* report) {
-  const int ni = (int)idx.size();
-  if (ni == 0) return SYK_OK;
-  KFn fn = kernel_for((int)B);
+  if (idx.empty()) return SYK_OK;
+  KFn fn = kernel_for((int)Bs);
   if (!fn) {
-    set_error("persistent batch: unsupported batch %lld", (long long)B);
+    set_error("persistent batch: unsupported states per CTA %lld", (long long)Bs);
     return SYK_EINVAL;
   }
-  // largest sectors first, so that the long items do not form the tail
-  std::vector<int> order(idx);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return items[x].terms->D > items[y].terms->D; });
-  long long vmax = 0;
-  for (int k : order) vmax = std::max<long long>(vmax, (long long)items[k].terms->D * B);
+  // sub-items (item, first column), largest sectors first so that the long ones do not form the tail
+  struct Sub {
+    int k;
+    int64_t b0;
+  };
+  std::vector<Sub> subs;
+  for (int k : idx)
+    for (int64_t b0 = 0; b0 < items[k].nstates; b0 += Bs) subs.push_back({k, b0});
+  std::stable_sort(subs.begin(), subs.end(),
+                   [&](const Sub& x, const Sub& y) { return items[x.k].terms->D > items[y.k].terms->D; });
+  const int ni = (int)subs.size();
+  long long vmax = 0, cmax = 0;
+  for (const Sub& u : subs) {
+    const syk_terms* T = items[u.k].terms;
+    vmax = std::max<long long>(vmax, (long long)T->D * Bs);
+    cmax = std::max<long long>(cmax, (long long)T->D * (1 + 2LL * T->n2));
+  }
   PLayout L;
-  if (!make_layout(vmax, (int)B, m, smem_optin_limit(), &L)) {
+  if (!make_layout(vmax, (int)Bs, m, smem_optin_limit(), &L)) {
     set_error("persistent batch: items do not fit in shared memory");
     return SYK_EINVAL;
   }
   const int grid = std::min(ni, sm_count());
   Scratch sc(st);
   void *d_items, *d_stat, *d_next, *d_t, *d_F, *d_ws;
+  size_t fsize = 0;  // device results: nt x nstates per item, in idx order
+  std::vector<size_t> foff(idx.size());
+  for (size_t q = 0; q < idx.size(); ++q) {
+    foff[q] = fsize;
+    fsize += (size_t)nt * items[idx[q]].nstates;
+  }
+  auto item_slot = [&](int k) {
+    return (size_t)(std::find(idx.begin(), idx.end(), k) - idx.begin());
+  };
   SYK_TRY(sc.alloc(&d_items, sizeof(PItem) * ni));
   SYK_TRY(sc.alloc(&d_stat, sizeof(long long) * kStWords * ni));
   SYK_TRY(sc.alloc(&d_next, sizeof(int)));
   SYK_TRY(sc.alloc(&d_t, sizeof(double) * nt));
-  SYK_TRY(sc.alloc(&d_F, sizeof(double2) * (size_t)nt * B * ni));
-  SYK_TRY(sc.alloc(&d_ws, sizeof(float2) * (size_t)vmax * (m + 5) * grid));
+  SYK_TRY(sc.alloc(&d_F, sizeof(double2) * fsize));
+  SYK_TRY(sc.alloc(&d_ws, sizeof(float2) * ((size_t)vmax * (m + 5) + (size_t)cmax) * grid));
   std::vector<PItem> h(ni);
+  std::vector<size_t> sub_slot(ni);
   for (int q = 0; q < ni; ++q) {
-    const syk_otoc_item& itm = items[order[q]];
+    const syk_otoc_item& itm = items[subs[q].k];
     const syk_terms* T = itm.terms;
+    const int64_t B = itm.nstates, b0 = subs[q].b0;
     ApplyParams P;
     SYK_TRY(make_apply_params(T, 0, SYK_C64, &P));
-    const void* psi = nullptr;
-    SYK_TRY(device_input(itm.psi0, sizeof(float2) * (size_t)T->D * B, sc, &psi));
+    void* psi = nullptr;
+    SYK_TRY(sc.alloc(&psi, sizeof(float2) * (size_t)T->D * Bs));
+    SYK_CUDA_CHECK(cudaMemcpy2DAsync(psi, sizeof(float2) * Bs, static_cast<const float2*>(itm.psi0) + b0,
+                                     sizeof(float2) * B, sizeof(float2) * Bs, (size_t)T->D, cudaMemcpyDefault, st));
+    sub_slot[q] = item_slot(subs[q].k);
     PItem& p = h[q];
     p.m4_rec = P.m4_rec;
     p.m4_t32 = static_cast<const float2*>(P.m4_tab);
@@ -805,18 +884,23 @@ int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& id
     p.m2_t32 = static_cast<const float2*>(P.m2_tab);
     p.wd32 = static_cast<const float*>(P.wd);
     p.psi0 = static_cast<const float2*>(psi);
-    p.F = static_cast<double2*>(d_F) + (size_t)q * nt * B;
+    p.F = static_cast<double2*>(d_F) + foff[sub_slot[q]] + b0;
+    p.Fld = (int)B;
     p.beta = itm.beta;
     p.rho = T->rho_est;
     p.n = T->n;
     p.D = (int)T->D;
     p.n4 = T->n4;
     p.n2 = T->n2;
-    // checks every ~(check cost / matvec cost) vectors: a check (FP64 eigensolve) ~0.3 ms,
-    // a matvec on one SM ~8 nnz B flop at 2e11 flop/s
-    const double mv_ms = 8.0 * double(T->D) * double(T->n4 + T->n2 + 1) * double(B) / 2.0e8;
-    p.every = std::max(2, std::min(8, (int)std::lround(0.3 / std::max(mv_ms, 1e-6))));
-    p.pad = 0;
+    // Check plan from the measured costs in this kernel: a convergence check (FP64 eigensolves
+    // of Bs columns sharing the SM's FP64 pipe) ~0.6 + 0.05 Bs ms; a matvec ~(0.10 + 0.035 Bs)
+    // ns per row x mask pair.  The later checks come every ~sqrt(16 ratio) vectors (the
+    // expected overshoot of a few vectors against the checks saved), the first at 3/4 of the
+    // predicted dimension when checks are cheap, 7/8 or all of it when they are not.
+    const double mv_ms = double(T->D) * double(T->n4 + T->n2 + 1) * (0.10 + 0.035 * double(Bs)) * 1e-6;
+    const double ratio = (0.6 + 0.05 * double(Bs)) / std::max(mv_ms, 1e-6);
+    p.every = std::max(2, std::min(8, (int)std::lround(std::sqrt(16.0 * ratio))));
+    p.first8 = ratio < 1.0 ? 6 : ratio < 4.0 ? 7 : 8;
   }
   SYK_CUDA_CHECK(cudaMemcpyAsync(d_items, h.data(), sizeof(PItem) * ni, cudaMemcpyHostToDevice, st));
   SYK_CUDA_CHECK(cudaMemcpyAsync(d_t, t, sizeof(double) * nt, cudaMemcpyHostToDevice, st));
@@ -834,6 +918,7 @@ int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& id
   a.bt = 64.0 * 5.96e-8;
   a.ws = static_cast<float2*>(d_ws);
   a.vmax = vmax;
+  a.cmax = cmax;
   a.L = L;
   SYK_TRY(ensure_smem_limit(reinterpret_cast<const void*>(fn), L.total));
   // the queue reset and the persistent launch, as one CUDA graph
@@ -858,7 +943,7 @@ int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& id
   const cudaError_t eg = cudaGraphLaunch(ge, st);
   count_launch(1);
   std::vector<long long> hst((size_t)kStWords * ni);
-  std::vector<double2> hF((size_t)nt * B * ni);
+  std::vector<double2> hF(fsize);
   cudaError_t e1 = eg;
   if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(hst.data(), d_stat, sizeof(long long) * hst.size(), cudaMemcpyDeviceToHost, st);
   if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(hF.data(), d_F, sizeof(double2) * hF.size(), cudaMemcpyDeviceToHost, st);
@@ -868,46 +953,49 @@ int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& id
     set_error("persistent batch: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     return SYK_ECUDA;
   }
-  int rc = SYK_OK;
-  long long mv_states = 0, bases = 0, cym = 0, cyc = 0, cye = 0, cya = 0;
+  // per item: the OR of its sub-items' error bits
+  std::vector<int> bits(idx.size(), 0);
+  long long tot[kStWords] = {};
   for (int q = 0; q < ni; ++q) {
-    const int k = order[q];
-    const long long* s = &hst[(size_t)q * kStWords];
-    const int bits = (int)s[kStStatus];
+    const long long* w = &hst[(size_t)q * kStWords];
+    bits[sub_slot[q]] |= (int)w[kStStatus];
+    for (int e = 1; e < kStWords; ++e) tot[e] += w[e];
+  }
+  int rc = SYK_OK;
+  for (size_t q = 0; q < idx.size(); ++q) {
+    const int k = idx[q];
     int irc = SYK_OK;
-    if (bits) {
+    if (bits[q]) {
       irc = SYK_ENUMERIC;
       if (rc == SYK_OK) {
         set_error("persistent batch: item %d: %s", k,
-                  (bits & 1) ? "non-finite Lanczos scalar"
-                             : (bits & 2) ? "tridiagonal eigensolver did not converge"
-                                          : "Krylov step collapsed or too many bases; raise krylov_dim or tol");
+                  (bits[q] & 1) ? "non-finite Lanczos scalar"
+                                : (bits[q] & 2) ? "tridiagonal eigensolver did not converge"
+                                                : "Krylov step collapsed or too many bases; raise krylov_dim or tol");
         rc = irc;
       }
     }
     if (item_status) item_status[k] = irc;
     double* F = items[k].F_re_im;
-    for (size_t e = 0; e < (size_t)nt * B; ++e) {
-      F[2 * e] = hF[(size_t)q * nt * B + e].x;
-      F[2 * e + 1] = hF[(size_t)q * nt * B + e].y;
+    const size_t ne = (size_t)nt * items[k].nstates;
+    for (size_t e = 0; e < ne; ++e) {
+      F[2 * e] = hF[foff[q] + e].x;
+      F[2 * e + 1] = hF[foff[q] + e].y;
     }
-    mv_states += s[kStMatvecs] * B;
-    bases += s[kStBases];
-    cym += s[kStCyMatvec];
-    cyc += s[kStCyCheck];
-    cye += s[kStCyEig];
-    cya += s[kStCyAll];
   }
-  count_applies(mv_states);
-  count_bases(bases);
+  count_applies(tot[kStMatvecs] * Bs);
+  count_bases(tot[kStBases]);
   if (report) {
-    report[0] += ni;
+    report[0] += (long long)idx.size();
+    report[10] += ni;
     report[2] += grid;
-    report[3] += cym;
-    report[4] += cyc;
-    report[5] += cye;
-    report[6] += cya;
-    report[7] += mv_states;
+    report[3] += tot[kStCyMatvec];
+    report[4] += tot[kStCyCheck];
+    report[5] += tot[kStCyEig];
+    report[6] += tot[kStCyAll];
+    report[7] += tot[kStMatvecs] * Bs;
+    report[8] += tot[kStChecks];
+    report[9] += tot[kStEigs];
   }
   return rc;
 }
@@ -925,8 +1013,8 @@ void batch_report_load(long long* r) {
 }  // namespace syk
 
 extern "C" int syk_batch_persistent(int on) {
-  if (on != 0 && on != 1) {
-    syk::set_error("syk_batch_persistent: mode must be 0 or 1 (got %d)", on);
+  if (on < 0 || on > 2) {
+    syk::set_error("syk_batch_persistent: mode must be 0, 1 or 2 (got %d)", on);
     return SYK_EINVAL;
   }
   return syk::g_persistent.exchange(on);

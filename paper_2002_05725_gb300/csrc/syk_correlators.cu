@@ -307,13 +307,26 @@ extern "C" int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int
   // items for the persistent launch, by batch size (1, 2, 4, 8, 16); the rest go to the workers
   std::vector<char> persistent(nitems, 0);
   std::vector<std::vector<int>> pgroups(5);
-  for (int k = 0; k < nitems; ++k)
-    if (batch_item_persistent_ok(items[k].terms, items[k].nstates, items[k].psi0, dtype, krylov_dim)) {
+  // Items whose states must be split over several CTAs (sector vectors too large for one CTA
+  // at their full state count) run 2 states per CTA, where a CTA's matvec is several times
+  // slower per state than the per-item path's full-GPU kernels; they pay off when their
+  // sub-items fill at least half the GPU, otherwise they stay on the streams.
+  std::vector<int> bsv(nitems, 0);
+  long long split_subitems = 0;
+  for (int k = 0; k < nitems; ++k) {
+    bsv[k] = batch_item_persistent_states(items[k].terms, items[k].nstates, items[k].psi0, dtype, krylov_dim);
+    if (bsv[k] > 0 && bsv[k] < items[k].nstates) split_subitems += items[k].nstates / bsv[k];
+  }
+  const bool take_split = 2 * split_subitems >= sm_count() || batch_persistent_split_always();
+  for (int k = 0; k < nitems; ++k) {
+    const int bs = bsv[k];
+    if (bs > 0 && (bs == items[k].nstates || take_split)) {
       persistent[k] = 1;
       int g = 0;
-      while ((int64_t(1) << g) < items[k].nstates) ++g;
+      while ((1 << g) < bs) ++g;
       pgroups[g].push_back(k);
     }
+  }
   long long report[kBatchReportWords] = {};
   // tune the matvec shape of every distinct (N, batch) once
   {

@@ -111,17 +111,21 @@ void* pinned_scratch(size_t bytes);
 int lanczos_begin(int dtype, const void* psi, KrylovWS& ws, cudaStream_t st);
 int lanczos_steps(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1, cudaStream_t st);
 
-// Persistent batched OTOC (syk_batch.cu).  batch_item_persistent_ok: the item can run in the
-// persistent kernel (complex64 with the three-term recurrence, a batch of 1, 2, 4, 8 or 16
-// states, its sector vector and the launch's scalars within one CTA's shared memory).
-// otoc_batch_persistent runs such items of one batch size as ONE launch on stream st and
-// fills their host results and statuses (synchronises st); report gets, added: items, -,
-// CTAs, clock cycles in matvecs, convergence checks, full eigendecompositions, all item work,
-// and H applications (states x matvecs).
-constexpr int kBatchReportWords = 8;
+// Persistent batched OTOC (syk_batch.cu).  batch_item_persistent_states: how many of an item's
+// states one CTA of the persistent kernel takes (1, 2, 4, 8 or 16: the largest power of two
+// that divides the item's state count and whose sector vectors and launch scalars fit one
+// CTA's shared memory; at least 2 unless the item has one state), or 0 when the item takes
+// the per-item path (complex128, full Gram-Schmidt for complex64, or too large a sector).
+// otoc_batch_persistent runs the items in idx, each split into sub-items of Bs states (one
+// CTA each; the states of a chain are independent), as ONE launch on stream st and fills their
+// host results and statuses (synchronises st); report gets, added: items, -, CTAs, clock
+// cycles in matvecs, convergence checks, full eigendecompositions and whole sub-items, H
+// applications (states x matvecs), convergence checks, full eigendecompositions, sub-items.
+constexpr int kBatchReportWords = 11;
 bool batch_persistent_enabled();
-bool batch_item_persistent_ok(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m);
-int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& idx, int64_t B, int i, int j,
+bool batch_persistent_split_always();  // syk_batch_persistent(2): split items regardless of count
+int batch_item_persistent_states(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m);
+int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& idx, int64_t Bs, int i, int j,
                           const double* t, int nt, int m, double tol, int* item_status, cudaStream_t st,
                           long long* report);
 void batch_report_store(const long long* r);

@@ -378,17 +378,21 @@ def syk_otoc_batch(items, i: int, j: int, times, dtype: int = SYK_C64, krylov_di
     return [F[..., 0] + 1j * F[..., 1] for F in outs]
 
 
-def syk_batch_persistent(on: bool = True) -> bool:
-    """Whether syk_otoc_batch runs the items that fit one CTA in its persistent launch; returns
-    the previous setting."""
-    rc = load().syk_batch_persistent(int(bool(on)))
+BATCH_STREAMS, BATCH_PERSISTENT, BATCH_PERSISTENT_SPLIT_ALWAYS = 0, 1, 2
+
+
+def syk_batch_persistent(mode=True) -> int:
+    """0 / False: every syk_otoc_batch item on the per-item streams; 1 / True: items that fit
+    run in the persistent launch (split items only in large batches); 2: split items always
+    go there too.  Returns the previous mode."""
+    rc = load().syk_batch_persistent(int(mode))
     if rc < 0:
         _check(rc, "syk_batch_persistent")
-    return bool(rc)
+    return rc
 
 
 BATCH_REPORT_KEYS = ("persistent_items", "stream_items", "persistent_ctas", "cycles_matvec", "cycles_check",
-                     "cycles_eig", "cycles_items", "h_applies")
+                     "cycles_eig", "cycles_items", "h_applies", "checks", "full_eigs", "persistent_subitems")
 
 
 def syk_batch_report() -> dict:

@@ -27,7 +27,15 @@ def _items(torch, spec, seed):
 
 @pytest.fixture
 def persistent_on():
-    prev = syk.syk_batch_persistent(True)
+    prev = syk.syk_batch_persistent(syk.BATCH_PERSISTENT)
+    yield
+    syk.syk_batch_persistent(prev)
+
+
+@pytest.fixture
+def persistent_split():
+    """Items split over several CTAs go to the persistent launch whatever the batch size."""
+    prev = syk.syk_batch_persistent(syk.BATCH_PERSISTENT_SPLIT_ALWAYS)
     yield
     syk.syk_batch_persistent(prev)
 
@@ -73,23 +81,55 @@ def test_persistent_matches_per_item_path_on_the_bench_grid(persistent_on):
         assert rel(Fp / Fp[0], Fr / Fr[0]) < TOL["c64"], (N, rel(Fp / Fp[0], Fr / Fr[0]))
 
 
-def test_persistent_and_per_item_items_in_one_batch(persistent_on):
-    """A batch mixing items for the persistent launch with items it cannot take (N = 28 at 8
-    states: its sector vector exceeds a CTA's shared memory) runs both paths concurrently."""
+def test_persistent_and_per_item_items_in_one_batch(persistent_split):
+    """A batch mixing items for the persistent launch -- N = 28 at 8 states is split into four
+    CTAs of 2 states, whose 2^13 x 2 sector vectors fit shared memory -- with one it cannot
+    take (N = 32 at 8 states: 2^14 rows per state even one state per CTA would exceed it),
+    which runs on the per-item streams concurrently."""
     torch = torch_or_skip()
     syk.load(build_if_missing=True)
     ts = [0.0, 1.0, 3.0]
-    spec = [(28, 8, 3.0), (20, 8, 3.0), (24, 4, 1.0)]
+    spec = [(32, 8, 3.0), (28, 8, 3.0), (20, 8, 3.0), (24, 4, 1.0)]
     items, raw = _items(torch, spec, seed=2)
     out = syk.syk_otoc_batch(items, 0, 1, ts, dtype=syk.SYK_C64, krylov_dim=30, tol=1e-7, nworkers=2)
     rep = syk.syk_batch_report()
-    assert rep["persistent_items"] == 2 and rep["stream_items"] == 1, rep
+    assert rep["persistent_items"] == 3 and rep["stream_items"] == 1, rep
+    assert rep["persistent_subitems"] == 4 + 1 + 1, rep
     for F, (terms, beta, x), (N, J, _, psi) in zip(out, items, raw):
         single = syk.syk_otoc(terms, beta, 0, 1, ts, x, krylov_dim=30, tol=1e-7)
         assert rel(F, single) < 5e-6, (N, rel(F, single))
         if N <= 24:
             Fr = co.F_state(evolve.SectorSystem(N, J), beta, 0, 1, ts, psi.T)
             assert rel(F / F[0], Fr / Fr[0]) < TOL["c64"], N
+
+
+def _golden_n28():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_N28_curves.json")) as f:
+        g = json.load(f)
+    F = np.array(g["F"]["values"])  # (state, t, re/im)
+    return g, (F[..., 0] + 1j * F[..., 1]).T  # (t, state)
+
+
+@pytest.mark.parametrize("B", [2, 8])
+def test_persistent_N28_vs_stored_oracle_curves(persistent_split, B):
+    """N = 28 (sector 2^13), beta J = 10, t = 0, 3, 6, 12 against the oracle's expm_multiply
+    curves stored by tests/golden/make_oracle_curves.py: 2 states (one CTA) and 8 states (four
+    CTAs of 2; the stored states are the first two of the seeded draw)."""
+    torch = torch_or_skip()
+    syk.load(build_if_missing=True)
+    g, Fref = _golden_n28()
+    J = inputs.couplings(28, g["seed"])
+    psi = inputs.random_states(28, B, g["seed"])
+    terms = syk.syk_build_terms(28, J)
+    F = syk.syk_otoc_batch([(terms, g["F"]["beta"], to_dev(torch, psi, "c64"))], 0, 1, g["t"], dtype=syk.SYK_C64,
+                           krylov_dim=40, tol=1e-7)[0]
+    rep = syk.syk_batch_report()
+    assert rep["persistent_items"] == 1 and rep["persistent_subitems"] == B // 2, rep
+    for s in range(2):
+        err = np.max(np.abs(F[:, s] - Fref[:, s])) / np.max(np.abs(Fref[:, s]))
+        assert err < TOL["c64"], (B, s, err)
 
 
 def test_persistent_reports_non_finite_items(persistent_on):
@@ -119,3 +159,15 @@ def test_persistent_reports_non_finite_items(persistent_on):
     Fr = co.F_state(evolve.SectorSystem(N, inputs.couplings(N, 1)), 1.0, 0, 1, ts, good.T)
     F0 = Fs[0][..., 0] + 1j * Fs[0][..., 1]
     assert rel(F0, Fr) < TOL["c64"]
+
+
+def test_split_items_stay_on_streams_in_small_batches(persistent_on):
+    """In the default mode a lone N = 28 item of 8 states (four CTAs of 2 states, far fewer
+    than half the SMs) takes the per-item path, while an N = 24 item of 8 states (one CTA)
+    takes the persistent launch."""
+    torch = torch_or_skip()
+    syk.load(build_if_missing=True)
+    items, _ = _items(torch, [(28, 8, 1.0), (24, 8, 1.0)], seed=4)
+    syk.syk_otoc_batch(items, 0, 1, [0.0, 0.5], dtype=syk.SYK_C64, krylov_dim=30, tol=1e-7)
+    rep = syk.syk_batch_report()
+    assert rep["persistent_items"] == 1 and rep["stream_items"] == 1 and rep["persistent_subitems"] == 1, rep
