@@ -32,6 +32,9 @@ constexpr int kPG = 64;                // popcount-4 masks staged in shared memo
 // evolution): past them the item stops with error bit 4, so no input keeps a CTA busy for long.
 constexpr int kMaxBasesPerEvolution = 1000;
 constexpr long long kMaxBasesPerItem = 4000;
+// Bisection steps of the step selection: the accepted step is within 2^-12 of the largest
+// admissible one (the per-item path takes 24; each costs an FP64 evaluation of the estimate).
+constexpr int kBisect = 12;
 
 // One work item: a coupling draw's tables (complex64 copies), its states and beta.
 struct PItem {
@@ -380,6 +383,8 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
                           const float2* pcs) {
   const int D = it.D, m = a.m, tid = threadIdx.x;
   const double tol = a.tol;
+  const size_t fstride = (size_t)m * m + 4 * (size_t)m + 2;  // doubles per column: Q, d, e, fg, rot
+  const bool fused = a.L.ncol >= B;
   if (zr == 0.0 && zi == 0.0) {
     if (out != in) cta_copy<B>(in, out, D);
     return;
@@ -513,28 +518,46 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
         }
         __syncthreads();
       }
-      // convergence check on T of dimension j1: warp b checks column b
+      // convergence check on T of dimension j1: warp b checks column b.  Fused (every column's
+      // eigenvector matrix fits region A at once): the check runs the full eigendecomposition,
+      // and the accepted basis takes its coefficients from it (on GB300 the FP64-bound
+      // rows-only and full eigensolves cost about the same); otherwise rows 0 and j1-1 only.
       {
         const long long t0 = clk();
         const int wp = tid >> 5, lane = tid & 31;
         if (wp < B) {
           const int b = wp;
-          double* d = reinterpret_cast<double*>(S.A) + (size_t)b * 4 * m;
-          double* e = d + m;
-          double* q0 = e + m;
-          double* qm = q0 + m;
-          for (int k = lane; k < j1; k += 32) {
-            d[k] = S.alpha[k * B + b];
-            e[k] = k + 1 < j1 ? S.beta[k * B + b] : 0.0;
-          }
-          __syncwarp();
+          double *d, *e, *q0, *qm;
           bool ok = true;
-          if (lane == 0) ok = tridiag_eig_rows(j1, d, e, q0, qm);
-          ok = __shfl_sync(0xffffffffu, ok, 0);
-          __syncwarp();
+          if (fused) {
+            double* Qm = reinterpret_cast<double*>(S.A) + (size_t)b * fstride;
+            d = Qm + (size_t)m * m;
+            e = d + m;
+            for (int k = lane; k < j1; k += 32) {
+              d[k] = S.alpha[k * B + b];
+              e[k] = k + 1 < j1 ? S.beta[k * B + b] : 0.0;
+            }
+            __syncwarp();
+            ok = tridiag_eig_warp(j1, d, e, Qm, e + 3 * m);
+            q0 = Qm;
+            qm = Qm + (size_t)(j1 - 1) * j1;
+          } else {
+            d = reinterpret_cast<double*>(S.A) + (size_t)b * 4 * m;
+            e = d + m;
+            q0 = e + m;
+            qm = q0 + m;
+            for (int k = lane; k < j1; k += 32) {
+              d[k] = S.alpha[k * B + b];
+              e[k] = k + 1 < j1 ? S.beta[k * B + b] : 0.0;
+            }
+            __syncwarp();
+            if (lane == 0) ok = tridiag_eig_rows(j1, d, e, q0, qm);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();
+          }
           if (!ok && lane == 0) atomicOr(&S.ctl->status, 2);
           const double bl = S.beta[(j1 - 1) * B + b];
-          const double s = select_step(j1, d, q0, qm, bl, s_rem, tol, zr, zi);
+          const double s = select_step(j1, d, q0, qm, bl, s_rem, tol, zr, zi, kBisect);
           if (lane == 0) S.sb[b] = s;
         }
         __syncthreads();
@@ -563,12 +586,12 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
       return;
     }
     const bool final_basis = s_acc >= s_rem || s_done + s_acc * (1.0 + 1e-13) >= 1.0;
-    // full eigendecomposition of the accepted basis and the combination coefficients
+    // full eigendecomposition of the accepted basis (unless the last check made it) and the
+    // combination coefficients
     //   cc[k][b] = beta0_b sum_l Q_b[k][l] e^{s_acc z theta_l} Q_b[0][l]   (as k_tridiag_coef)
     {
       const long long t0 = clk();
       const int wp = tid >> 5, lane = tid & 31;
-      const size_t fstride = (size_t)m * m + 4 * (size_t)m + 2;
       for (int r0 = 0; r0 < B; r0 += a.L.ncol) {
         const int b = r0 + wp;
         if (wp < a.L.ncol && b < B) {
@@ -577,13 +600,15 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
           double* e = d + m;
           double* fg = e + m;     // 2 m doubles
           double* rot = fg + 2 * m;
-          for (int k = lane; k < m_eff; k += 32) {
-            d[k] = S.alpha[k * B + b];
-            e[k] = k + 1 < m_eff ? S.beta[k * B + b] : 0.0;
+          if (!fused) {
+            for (int k = lane; k < m_eff; k += 32) {
+              d[k] = S.alpha[k * B + b];
+              e[k] = k + 1 < m_eff ? S.beta[k * B + b] : 0.0;
+            }
+            __syncwarp();
+            const bool ok = tridiag_eig_warp(m_eff, d, e, Qm, rot);
+            if (!ok && lane == 0) atomicOr(&S.ctl->status, 2);
           }
-          __syncwarp();
-          const bool ok = tridiag_eig_warp(m_eff, d, e, Qm, rot);
-          if (!ok && lane == 0) atomicOr(&S.ctl->status, 2);
           for (int l = lane; l < m_eff; l += 32) {
             const double2 f = cexp_scaled(s_acc, zr, zi, d[l]);
             const double g = Qm[l];  // row 0
@@ -605,7 +630,7 @@ __device__ __noinline__ void cta_expmv(const PArgs& a, const PItem& it, int sect
         __syncthreads();
       }
       pc.cy[2] += clk() - t0;
-      ++pc.neig;
+      if (!fused) ++pc.neig;
     }
     if (S.ctl->status & 3) return;
     for (int e = tid; e < m_eff * B; e += kPNT) {

@@ -170,10 +170,10 @@ static __device__ double step_error(int m, const double* d, const double* q0, co
 }
 
 // The largest step s <= s_target whose estimate step_error is <= tol: halve s until the
-// estimate passes (at most 80 times), then bisect 24 times between the last failing and the
+// estimate passes (at most 80 times), then bisect nbis times between the last failing and the
 // first passing step.  Every lane of the warp calls it (step_error sums over the lanes).
 static __device__ double select_step(int m, const double* d, const double* q0, const double* qm, double bl,
-                                     double s_target, double tol, double zr, double zi) {
+                                     double s_target, double tol, double zr, double zi, int nbis = 24) {
   double s = s_target;
   if (step_error(m, d, q0, qm, bl, s, zr, zi) > tol) {
     double lo = 0.0, hi = s;
@@ -185,7 +185,7 @@ static __device__ double select_step(int m, const double* d, const double* q0, c
       ++it;
     }
     lo = s;
-    for (int k = 0; k < 24; ++k) {  // largest admissible step within [lo, hi)
+    for (int k = 0; k < nbis; ++k) {  // largest admissible step within [lo, hi)
       const double mid = 0.5 * (lo + hi);
       if (step_error(m, d, q0, qm, bl, mid, zr, zi) <= tol) lo = mid;
       else hi = mid;
