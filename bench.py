@@ -560,6 +560,14 @@ def run_batched(a, rank, world, local_rank, draws):
                   "seconds_per_subitem": rep["cycles_items"] / hz / max(rep["persistent_subitems"], 1),
                   "ms_per_check": rep["cycles_check"] / hz * 1e3 / max(rep["checks"], 1),
                   "ms_per_full_eig": rep["cycles_eig"] / hz * 1e3 / max(rep["full_eigs"], 1),
+                  # the CTAs' matvec rate per SM against the FP32 lane rate of one SM (128 lanes x 2
+                  # flop x clock): algorithmic flops (8 per nonzero of H_s per state) over the
+                  # clock cycles the CTAs spent in matvecs
+                  "matvec_roofline": {
+                      "achieved_tflops_per_sm": rep["matvec_flops"] / max(rep["cycles_matvec"] / hz, 1e-30) / 1e12,
+                      "peak_tflops_per_sm": 128 * 2 * hz / 1e12,
+                      "frac": rep["matvec_flops"] / max(rep["cycles_matvec"], 1) / 256.0,
+                      "peak_kind": "unit count (128 FP32 lanes x 2 flop per cycle per SM)"},
                   "cycle_shares": {"matvec": rep["cycles_matvec"] / cyc, "convergence_checks": rep["cycles_check"] / cyc,
                                    "full_eigendecompositions": rep["cycles_eig"] / cyc},
                   "note": "items whose sector vector fits one CTA's shared memory run as one persistent launch "

@@ -265,13 +265,14 @@ int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const d
  * Plumbing; no counterpart in the paper. */
 int syk_batch_persistent(int on);
 /* syk_batch_report -- counters of the last syk_otoc_batch call (host array of
- * n <= 11 words): items in the persistent launch, items on the per-item path,
+ * n <= 12 words): items in the persistent launch, items on the per-item path,
  * CTAs of the persistent launch; summed over its sub-items (one CTA's share of
  * an item's states): SM clock cycles spent in matvecs, in convergence checks
  * (tridiagonal eigenvalues and step selection), in the full
  * eigendecompositions of accepted bases and in whole sub-items; H applications
- * (states x matvecs), convergence checks, full eigendecompositions; and the
- * number of sub-items.  Measurement; no counterpart in the paper. */
+ * (states x matvecs), convergence checks, full eigendecompositions; the
+ * number of sub-items; and the matvecs' algorithmic flops (8 per nonzero of the
+ * sector Hamiltonian per state).  Measurement; no counterpart in the paper. */
 int syk_batch_report(long long* out, int n);
 
 /* --------------------------------------------------------------- gradients

@@ -981,10 +981,13 @@ int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& id
   // per item: the OR of its sub-items' error bits
   std::vector<int> bits(idx.size(), 0);
   long long tot[kStWords] = {};
+  long long mv_flops = 0;  // algorithmic matvec work: 8 flops per nonzero of H_s per state
   for (int q = 0; q < ni; ++q) {
     const long long* w = &hst[(size_t)q * kStWords];
     bits[sub_slot[q]] |= (int)w[kStStatus];
     for (int e = 1; e < kStWords; ++e) tot[e] += w[e];
+    const syk_terms* T = items[subs[q].k].terms;
+    mv_flops += w[kStMatvecs] * 8LL * T->D * (long long)(T->n4 + T->n2 + 1) * Bs;
   }
   int rc = SYK_OK;
   for (size_t q = 0; q < idx.size(); ++q) {
@@ -1013,6 +1016,7 @@ int otoc_batch_persistent(const syk_otoc_item* items, const std::vector<int>& id
   if (report) {
     report[0] += (long long)idx.size();
     report[10] += ni;
+    report[11] += mv_flops;
     report[2] += grid;
     report[3] += tot[kStCyMatvec];
     report[4] += tot[kStCyCheck];

@@ -120,8 +120,9 @@ int lanczos_steps(const ApplyParams& P, int dtype, KrylovWS& ws, int j0, int j1,
 // CTA each; the states of a chain are independent), as ONE launch on stream st and fills their
 // host results and statuses (synchronises st); report gets, added: items, -, CTAs, clock
 // cycles in matvecs, convergence checks, full eigendecompositions and whole sub-items, H
-// applications (states x matvecs), convergence checks, full eigendecompositions, sub-items.
-constexpr int kBatchReportWords = 11;
+// applications (states x matvecs), convergence checks, full eigendecompositions, sub-items,
+// and the matvecs' algorithmic flops (8 per nonzero of H_s per state).
+constexpr int kBatchReportWords = 12;
 bool batch_persistent_enabled();
 bool batch_persistent_split_always();  // syk_batch_persistent(2): split items regardless of count
 int batch_item_persistent_states(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m);

@@ -392,7 +392,8 @@ def syk_batch_persistent(mode=True) -> int:
 
 
 BATCH_REPORT_KEYS = ("persistent_items", "stream_items", "persistent_ctas", "cycles_matvec", "cycles_check",
-                     "cycles_eig", "cycles_items", "h_applies", "checks", "full_eigs", "persistent_subitems")
+                     "cycles_eig", "cycles_items", "h_applies", "checks", "full_eigs", "persistent_subitems",
+                     "matvec_flops")
 
 
 def syk_batch_report() -> dict:
