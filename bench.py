@@ -514,6 +514,33 @@ def gpu_main(a, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def persistent_summary(rep, hz):
+    """The `persistent` object of a --batched line from syk_batch_report's counters: where the
+    persistent launch's CTAs spent their SM clock cycles (hz: the SM clock sampled during the
+    run), and their matvec rate per SM against one SM's FP32 lane rate (128 lanes x 2 flop per
+    cycle): algorithmic flops (8 per nonzero of H_s per state) over the cycles in matvecs.
+    Convergence checks that run the full eigendecomposition leave no separate ones
+    (ms_per_full_eig None); the last share then holds only the combination coefficients."""
+    cyc = max(rep["cycles_items"], 1)
+    return {"items": rep["persistent_items"], "per_item_path_items": rep["stream_items"],
+            "subitems": rep["persistent_subitems"], "ctas": rep["persistent_ctas"],
+            "h_applies": rep["h_applies"], "convergence_checks": rep["checks"],
+            "full_eigendecompositions": rep["full_eigs"],
+            "seconds_per_subitem": rep["cycles_items"] / hz / max(rep["persistent_subitems"], 1),
+            "ms_per_check": rep["cycles_check"] / hz * 1e3 / rep["checks"] if rep["checks"] else None,
+            "ms_per_full_eig": rep["cycles_eig"] / hz * 1e3 / rep["full_eigs"] if rep["full_eigs"] else None,
+            "matvec_roofline": {
+                "achieved_tflops_per_sm": rep["matvec_flops"] * hz / max(rep["cycles_matvec"], 1) / 1e12,
+                "peak_tflops_per_sm": 128 * 2 * hz / 1e12,
+                "frac": rep["matvec_flops"] / max(rep["cycles_matvec"], 1) / 256.0,
+                "peak_kind": "unit count (128 FP32 lanes x 2 flop per cycle per SM)"},
+            "cycle_shares": {"matvec": rep["cycles_matvec"] / cyc, "convergence_checks": rep["cycles_check"] / cyc,
+                             "eigendecompositions_and_coefficients": rep["cycles_eig"] / cyc},
+            "note": "items whose sector vector fits one CTA's shared memory (or whose states split over CTAs) "
+                    "run as one persistent launch, a CTA per sub-item running its whole chain on the device; "
+                    "cycle shares are SM clock cycles summed over those sub-items"}
+
+
 def run_batched(a, rank, world, local_rank, draws):
     """Mixed-N batch: draws x (N in 20..40) x (beta J in 1, 3, 10), 8 states each, 10 points to t=12.
     Returns the throughput figure (curves/hour over the wall time of one syk_otoc_batch call)."""
@@ -551,28 +578,7 @@ def run_batched(a, rank, world, local_rank, draws):
     syk.syk_use_graphs(True)
     syk.syk_batch_persistent(prev_persistent)
     curves = 8 * len(items)
-    cyc = max(rep["cycles_items"], 1)
-    hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
-    persistent = {"items": rep["persistent_items"], "per_item_path_items": rep["stream_items"],
-                  "subitems": rep["persistent_subitems"], "ctas": rep["persistent_ctas"],
-                  "h_applies": rep["h_applies"], "convergence_checks": rep["checks"],
-                  "full_eigendecompositions": rep["full_eigs"],
-                  "seconds_per_subitem": rep["cycles_items"] / hz / max(rep["persistent_subitems"], 1),
-                  "ms_per_check": rep["cycles_check"] / hz * 1e3 / max(rep["checks"], 1),
-                  "ms_per_full_eig": rep["cycles_eig"] / hz * 1e3 / max(rep["full_eigs"], 1),
-                  # the CTAs' matvec rate per SM against the FP32 lane rate of one SM (128 lanes x 2
-                  # flop x clock): algorithmic flops (8 per nonzero of H_s per state) over the
-                  # clock cycles the CTAs spent in matvecs
-                  "matvec_roofline": {
-                      "achieved_tflops_per_sm": rep["matvec_flops"] / max(rep["cycles_matvec"] / hz, 1e-30) / 1e12,
-                      "peak_tflops_per_sm": 128 * 2 * hz / 1e12,
-                      "frac": rep["matvec_flops"] / max(rep["cycles_matvec"], 1) / 256.0,
-                      "peak_kind": "unit count (128 FP32 lanes x 2 flop per cycle per SM)"},
-                  "cycle_shares": {"matvec": rep["cycles_matvec"] / cyc, "convergence_checks": rep["cycles_check"] / cyc,
-                                   "full_eigendecompositions": rep["cycles_eig"] / cyc},
-                  "note": "items whose sector vector fits one CTA's shared memory run as one persistent launch "
-                          "(a CTA per item, the whole chain on the device); cycle shares are SM clock cycles "
-                          "summed over those items"}
+    persistent = persistent_summary(rep, (clocks.get("sm_mhz") or 2070.0) * 1e6)
     return {"metric": "OTOC curves/hour, mixed-N batch", "value": world * curves * 3600.0 / wall,
             "unit": "curves/hour", "wall_s": wall, "dtype": "c64",
             "config": {"workload": f"{draws} draw(s) x N in {Ns} x beta J in {betas}, 8 states each, "

@@ -63,3 +63,20 @@ def test_curve_error_is_per_state_max_t_norm():
     F[3, 1] += 2e-3 * 2.0  # state 1: F~ off by 2e-3 at one time, max_t |F~ref| = 1
     assert bench.curve_error(F, ref) == pytest.approx(2e-3)
     assert bench.curve_error(3.0 * ref, ref) == pytest.approx(0.0, abs=1e-15)  # scale cancels in F~
+
+
+def test_persistent_summary_shares_and_matvec_rate():
+    """The --batched line's persistent object from syk_batch_report counters: shares of the
+    CTAs' cycles, per-check time, and the matvec rate per SM against 128 lanes x 2 flop x clock."""
+    hz = 2.0e9
+    rep = {"persistent_items": 4, "stream_items": 1, "persistent_subitems": 8, "persistent_ctas": 8,
+           "cycles_matvec": 6e9, "cycles_check": 2e9, "cycles_eig": 0, "cycles_items": 8e9,
+           "h_applies": 1000, "checks": 400, "full_eigs": 0, "matvec_flops": int(0.25 * 256 * 6e9)}
+    p = bench.persistent_summary(rep, hz)
+    assert p["seconds_per_subitem"] == pytest.approx(8e9 / hz / 8)
+    assert p["ms_per_check"] == pytest.approx(2e9 / hz * 1e3 / 400)
+    assert p["ms_per_full_eig"] is None  # checks fused with the full eigendecomposition
+    assert p["cycle_shares"]["matvec"] == pytest.approx(0.75)
+    assert p["matvec_roofline"]["frac"] == pytest.approx(0.25)
+    assert p["matvec_roofline"]["achieved_tflops_per_sm"] == pytest.approx(0.25 * 256 * hz / 1e12)
+    assert p["matvec_roofline"]["peak_tflops_per_sm"] == pytest.approx(256 * hz / 1e12)
