@@ -4,12 +4,14 @@
 // by Eq. q_typicality, the chain of syk_otoc) by itself: every Krylov evolution (Supp. Sec.
 // I.B: Lanczos with the three-term recurrence, FP64 scalars, FP64 tridiagonal
 // eigendecompositions, Saad's error estimate and the step control of syk_expmv), the
-// Majorana applications and the final dots.  The item's sector vector fits in shared memory,
-// so every matvec gathers its partner rows psi[x ^ m] from the staged input; the Krylov basis
-// and the chain's vectors live in the CTA's own slice of global memory (L2).  CTAs share
-// nothing but the queue counter: there is no grid-wide synchronisation and no host round
-// trip until the launch ends.  complex64 vectors (FP32 arithmetic), as the batched workload
-// specifies; larger sectors and complex128 items take the per-item path of syk_otoc_batch.
+// Majorana applications and the final dots.  A work item is a sub-item: some of a coupling
+// draw's states (all of them, or a share of 2 or more when D x states would not fit), whose
+// sector vector fits in shared memory, so every matvec gathers its partner rows psi[x ^ m]
+// from the staged input; the Krylov basis and the chain's vectors live in the CTA's own slice
+// of global memory (L2).  CTAs share nothing but the queue counter: there is no grid-wide
+// synchronisation, no spin-wait (only CTA barriers) and no host round trip until the launch
+// ends.  complex64 vectors (FP32 arithmetic), as the batched workload specifies; larger
+// sectors and complex128 items take the per-item path of syk_otoc_batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
