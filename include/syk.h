@@ -268,9 +268,10 @@ int syk_batch_persistent(int on);
  * n <= 12 words): items in the persistent launch, items on the per-item path,
  * CTAs of the persistent launch; summed over its sub-items (one CTA's share of
  * an item's states): SM clock cycles spent in matvecs, in convergence checks
- * (tridiagonal eigenvalues and step selection), in the full
- * eigendecompositions of accepted bases and in whole sub-items; H applications
- * (states x matvecs), convergence checks, full eigendecompositions; the
+ * (tridiagonal eigendecompositions and step selection), in the combination
+ * coefficients of accepted bases (with their full eigendecomposition when no
+ * check computed it) and in whole sub-items; H applications (states x
+ * matvecs), convergence checks, separate full eigendecompositions; the
  * number of sub-items; and the matvecs' algorithmic flops (8 per nonzero of the
  * sector Hamiltonian per state).  Measurement; no counterpart in the paper. */
 int syk_batch_report(long long* out, int n);
