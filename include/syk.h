@@ -264,6 +264,17 @@ int syk_otoc_batch(const syk_otoc_item* items, int nitems, int i, int j, const d
  * 0: every item takes the per-item path.  Returns the previous mode.
  * Plumbing; no counterpart in the paper. */
 int syk_batch_persistent(int on);
+/* syk_batch_plan -- how syk_otoc_batch's persistent launch would take a complex64
+ * item of N Majoranas with nstates states at Krylov dimension krylov_dim, given
+ * smem_limit bytes of shared memory per CTA (<= 0: the current device's opt-in
+ * limit): *states_per_cta = the states one CTA takes (a power of two <= 16 that
+ * divides nstates; 1 only for one-state items), 0 when the item takes the
+ * per-item path; *smem_per_cta (may be NULL) = that launch's shared memory per
+ * CTA.  Host arithmetic only (no device needed when smem_limit > 0); whether a
+ * split item actually goes to the persistent launch also depends on the batch
+ * (see syk_otoc_batch).  Plumbing; no counterpart in the paper. */
+int syk_batch_plan(int N, int64_t nstates, int krylov_dim, int smem_limit, int* states_per_cta,
+                   int* smem_per_cta);
 /* syk_batch_report -- counters of the last syk_otoc_batch call (host array of
  * n <= 12 words): items in the persistent launch, items on the per-item path,
  * CTAs of the persistent launch; summed over its sub-items (one CTA's share of

@@ -826,17 +826,27 @@ int smem_optin_limit() {
   return v;
 }
 
-int batch_item_persistent_states(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m) {
-  if (!batch_persistent_enabled() || dtype != SYK_C64 || lanczos_orth(SYK_C64) != kOrthLocal) return 0;
-  (void)psi0;  // every sub-item gets its own aligned device copy of its columns
-  if (B < 1 || t->n < 2) return 0;
-  const int limit = smem_optin_limit();
+// States per CTA of the persistent launch for an item of n spins (sector dimension D) with B
+// states, Krylov dimension m and `limit` bytes of shared memory per CTA: the largest power of
+// two bs <= 16 dividing B whose layout fits (bs = 1 only for one-state items); 0 if none.
+// *smem gets that layout's bytes.  Host arithmetic only.
+int persistent_states_for(int64_t D, int n, int64_t B, int m, int limit, int* smem) {
+  if (B < 1 || n < 2) return 0;
   for (int bs = 16; bs >= 1; bs >>= 1) {
     if (B % bs != 0 || (bs == 1 && B > 1)) continue;
     PLayout L;
-    if (make_layout((long long)t->D * bs, bs, m, limit, &L)) return bs;
+    if (make_layout((long long)D * bs, bs, m, limit, &L)) {
+      if (smem) *smem = L.total;
+      return bs;
+    }
   }
   return 0;
+}
+
+int batch_item_persistent_states(const syk_terms* t, int64_t B, const void* psi0, int dtype, int m) {
+  if (!batch_persistent_enabled() || dtype != SYK_C64 || lanczos_orth(SYK_C64) != kOrthLocal) return 0;
+  (void)psi0;  // every sub-item gets its own aligned device copy of its columns
+  return persistent_states_for(t->D, t->n, B, m, smem_optin_limit(), nullptr);
 }
 
 // Runs the items of idx, each split into sub-items of Bs states (columns b0 .. b0 + Bs - 1 of
@@ -1049,6 +1059,22 @@ extern "C" int syk_batch_persistent(int on) {
     return SYK_EINVAL;
   }
   return syk::g_persistent.exchange(on);
+}
+
+extern "C" int syk_batch_plan(int N, int64_t nstates, int krylov_dim, int smem_limit, int* states_per_cta,
+                              int* smem_per_cta) {
+  if (N < 4 || N > 62 || (N & 1) || nstates < 1 || krylov_dim < 2 || krylov_dim > SYK_MAX_KRYLOV ||
+      !states_per_cta) {
+    syk::set_error("syk_batch_plan: need even 4 <= N <= 62, nstates >= 1, 2 <= krylov_dim <= %d and an output",
+                   SYK_MAX_KRYLOV);
+    return SYK_EINVAL;
+  }
+  const int n = N / 2;
+  const int limit = smem_limit > 0 ? smem_limit : syk::smem_optin_limit();
+  int smem = 0;
+  *states_per_cta = syk::persistent_states_for(int64_t(1) << (n - 1), n, nstates, krylov_dim, limit, &smem);
+  if (smem_per_cta) *smem_per_cta = *states_per_cta > 0 ? smem : 0;
+  return SYK_OK;
 }
 
 extern "C" int syk_batch_report(long long* out, int n) {

@@ -81,6 +81,7 @@ def load(build_if_missing: bool = False):
         "syk_lanczos_orth": (i32, [i32, i32]),
         "syk_batch_persistent": (i32, [i32]),
         "syk_batch_report": (i32, [vp, i32]),
+        "syk_batch_plan": (i32, [i32, i64, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -99,7 +100,7 @@ def exported_symbols():
             "syk_correlator_G_grad", "syk_otoc_batch", "syk_use_graphs", "syk_otoc_split",
             "syk_correlator_G_imag", "syk_autotune_reset", "syk_lowest_eigenvalues", "syk_fma_peak",
             "syk_matvec_launches", "syk_c128_arith", "syk_status", "syk_lanczos_orth", "syk_batch_persistent",
-            "syk_batch_report"]
+            "syk_batch_report", "syk_batch_plan"]
 
 
 def _check(rc: int, what: str):
@@ -389,6 +390,15 @@ def syk_batch_persistent(mode=True) -> int:
     if rc < 0:
         _check(rc, "syk_batch_persistent")
     return rc
+
+
+def syk_batch_plan(N: int, nstates: int, krylov_dim: int = 40, smem_limit: int = 0):
+    """(states per CTA, shared memory per CTA) of the persistent launch for a complex64 item;
+    states per CTA 0 means the per-item path.  smem_limit <= 0: the current device's limit."""
+    bs, sm = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().syk_batch_plan(int(N), int(nstates), int(krylov_dim), int(smem_limit), ctypes.byref(bs),
+                                 ctypes.byref(sm)), "syk_batch_plan")
+    return bs.value, sm.value
 
 
 BATCH_REPORT_KEYS = ("persistent_items", "stream_items", "persistent_ctas", "cycles_matvec", "cycles_check",
